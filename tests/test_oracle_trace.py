@@ -1,0 +1,209 @@
+"""Pins for the oracle's ray tracer (Sec. 3.3, 4.2-4.3, 5.2) and refinement.
+
+- Integration and event location agree with scipy's ``solve_ivp(RK45)``, an
+  independent Dormand-Prince 5(4) implementation with its own event finder.
+- Conserved quantities (Carter-like K of Eq. 56, null constraint Eq. 54).
+- Kerr capture classification is exact against the textbook radial potential
+  (Bardeen 1973; the paper validates its pipeline on the Kerr critical curve,
+  Sec. 4.1); Schwarzschild capture iff K/E^2 < 27.
+- Symmetries: equatorial observer mirror symmetry.
+- Intensity: g^3 j at the recorded crossing against the Kerr closed forms.
+- Refinement: per-pixel recomputation equals the whole-image result, and a
+  refined pixel equals the mean of its 16 children.
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+def kerr_radial_capture(a, E, ell, K, r_plus, r_obs):
+    """Textbook Kerr test: the ray from r_obs inward is captured iff the radial
+    potential R(r) = (r^2 + a^2 - a xi)^2 - Delta(r) K/E^2 stays positive on
+    (r_+, r_obs).  Returns (captured, min R / r^4 margin)."""
+    xi = ell / E
+    k = K / (E * E)
+
+    def Rpot(r):
+        return (r * r + a * a - a * xi) ** 2 - (r * r - 2 * r + a * a) * k
+
+    rs = np.concatenate([np.linspace(r_plus * (1 + 1e-9), 12.0, 20000), np.linspace(12.0, r_obs, 2000)])
+    v = Rpot(rs) / rs ** 4
+    i = int(np.argmin(v))
+    lo, hi = rs[max(i - 1, 0)], rs[min(i + 1, len(rs) - 1)]
+    gr = 0.5 * (math.sqrt(5) - 1)
+    for _ in range(100):
+        x1, x2 = hi - gr * (hi - lo), lo + gr * (hi - lo)
+        if Rpot(x1) / x1 ** 4 < Rpot(x2) / x2 ** 4:
+            hi = x2
+        else:
+            lo = x1
+    rm = 0.5 * (lo + hi)
+    m = min(Rpot(rm) / rm ** 4, v[i])
+    return m > 0, m
+
+
+@pytest.mark.parametrize("incl", [17.0, 60.0])
+def test_kerr_capture_matches_radial_potential(oracle, incl):
+    a = 0.5
+    P = oracle.problem(metric=oracle.KERR, chi=a, incl=math.radians(incl))
+    geo = oracle.geometry(P)
+    rng = np.random.default_rng(11)
+    # points concentrated around the shadow edge (radius ~ 5 M)
+    b = 3.5 + 3.0 * rng.random(120)
+    psi = 2 * math.pi * rng.random(120)
+    xy = np.stack([b * np.cos(psi), b * np.sin(psi)], 1)
+    rays = oracle.trace_points(P, xy)
+    checked = 0
+    for r in rays:
+        cap, margin = kerr_radial_capture(a, r["E"], r["ell"], r["K0"], geo["r_plus"], P.r_obs)
+        if abs(margin) < 1e-7:
+            continue
+        assert r["status"] == (1 if cap else 0)
+        checked += 1
+    assert checked > 100
+
+
+def test_schwarzschild_capture_is_rotationally_symmetric(oracle):
+    P = oracle.problem(metric=oracle.KERR, chi=0.0, incl=math.radians(30.0))
+    rng = np.random.default_rng(5)
+    b = 4.6 + 1.2 * rng.random(80)
+    psi = 2 * math.pi * rng.random(80)
+    rays = oracle.trace_points(P, np.stack([b * np.cos(psi), b * np.sin(psi)], 1))
+    for r in rays:
+        k = r["K0"] / r["E"] ** 2
+        if abs(k - 27.0) < 1e-6:
+            continue
+        assert r["status"] == (1 if k < 27.0 else 0)
+
+
+def test_conserved_quantities(oracle):
+    """Carter-like K (Eq. 56) and the null constraint (Eq. 54) at a tightened
+    tolerance: relative drift below 1e-10."""
+    for metric, kw in [(0, {}), (1, dict(lam_E=0.1)), (2, dict(eta=0.02))]:
+        P = oracle.problem(metric=metric, chi=0.9, incl=math.radians(80.0), rtol=1e-12,
+                           atol=1e-14, **kw)
+        rays = oracle.trace_points(P, [[2.0, 3.0], [-6.0, 1.0], [7.5, -6.5], [0.7, 5.5]])
+        for r in rays:
+            assert abs(r["K_final"] - r["K0"]) <= 1e-10 * abs(r["K0"])
+            assert r["h_drift"] < 1e-10
+
+
+def test_equatorial_observer_mirror_symmetry(oracle):
+    P = oracle.problem(metric=oracle.CNFW, chi=0.9, incl=math.pi / 2)
+    pts = np.array([[3.0, 2.5], [-5.0, 4.0], [8.0, 1.0], [-2.0, 6.5], [4.5, 0.3]])
+    up = oracle.trace_points(P, pts)
+    dn = oracle.trace_points(P, pts * np.array([1.0, -1.0]))
+    for a, b in zip(up, dn):
+        assert a["status"] == b["status"] and a["ncross"] == b["ncross"]
+        n = min(a["ncross"], 3)
+        assert np.allclose(a["R_em"][:n], b["R_em"][:n], rtol=1e-7)
+        assert a["I_tot"] == pytest.approx(b["I_tot"], rel=1e-6, abs=1e-12)
+
+
+def test_crossing_intensity_matches_kerr_closed_forms(oracle):
+    a = 0.5
+    P = oracle.problem(metric=oracle.KERR, chi=a, incl=math.radians(17.0))
+    geo = oracle.geometry(P)
+    rays = oracle.trace_points(P, [[6.0, 1.0], [-7.0, -3.0], [2.0, 8.0]])
+    for r in rays:
+        assert r["ncross"] >= 1
+        for n in range(min(r["ncross"], 3)):
+            R = r["R_em"][n]
+            x = R ** 1.5
+            W = 1 / (x + a)
+            uT = (x + a) / math.sqrt(x * (x - 3 * math.sqrt(R) + 2 * a))
+            g = 1 / (uT * (r["E"] - W * r["ell"]))
+            assert r["g"][n] == pytest.approx(g, rel=1e-11)
+            j = oracle.emissivity(P, geo["R_in"], R, math.pi / 2)
+            assert r["I_n"][n] == pytest.approx(g ** 3 * j, rel=1e-11)
+
+
+def test_trace_agrees_with_scipy_rk45(oracle):
+    """Same method (DP5(4), same error norm and controller constants),
+    independent implementation: the crossings and fates agree."""
+    integ = pytest.importorskip("scipy.integrate")
+    P = oracle.problem(metric=oracle.CNFW, chi=0.9, incl=math.radians(50.0))
+    geo = oracle.geometry(P)
+    pts = [[6.0, 1.0], [-5.0, -3.0], [2.0, 7.0], [9.0, -9.0], [-1.5, 2.0], [0.8, -6.2]]
+    rays = oracle.trace_points(P, pts)
+    for (X, Y), r in zip(pts, rays):
+        L = oracle.launch(P, X, Y)
+        E, ell = L["E"], L["ell"]
+
+        def f(t, y):
+            return oracle.rhs(P, E, ell, y)
+
+        def cross(t, y):
+            return y[2] - math.pi / 2
+
+        def cap(t, y):
+            return y[1] - geo["R_cap"]
+
+        def esc(t, y):
+            return y[1] - geo["R_esc"]
+
+        cap.terminal = True
+        esc.terminal = True
+        sol = integ.solve_ivp(f, (0.0, 1e5), L["y0"], method="RK45", rtol=P.rtol, atol=P.atol,
+                              events=[cross, cap, esc])
+        status = 1 if len(sol.t_events[1]) else (0 if len(sol.t_events[2]) else 2)
+        assert status == r["status"]
+        nc = len(sol.t_events[0])
+        assert nc == r["ncross"]
+        for n in range(min(nc, 3)):
+            assert sol.y_events[0][n][1] == pytest.approx(r["R_em"][n], rel=1e-7)
+            assert sol.t_events[0][n] == pytest.approx(r["lam_cross"][n], rel=1e-8)
+
+
+def test_eta_zero_cored_nfw_image_is_kerr_bitwise(oracle):
+    kw = dict(chi=0.6, incl=math.radians(40.0), nx=12, ny=12, levels=0)
+    a = oracle.trace_image(oracle.problem(metric=oracle.KERR, **kw))
+    b = oracle.trace_image(oracle.problem(metric=oracle.CNFW, eta=0.0, lam_c=10.0, **kw))
+    for k in ("I", "ncross", "status", "R_em", "g"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_refined_pixel_is_mean_of_children(oracle):
+    P = oracle.problem(chi=0.5, nx=16, ny=16, levels=1)
+    img = oracle.trace_image(P)
+    dx = (P.x_max - P.x_min) / P.nx
+    refined = np.argwhere(img["level"] == 1)
+    assert len(refined) > 0
+    j, i = refined[len(refined) // 2]
+    Xc, Yc = P.x_min + (i + 0.5) * dx, P.y_min + (j + 0.5) * dx
+    offs = (np.arange(4) + 0.5) / 4 - 0.5
+    xy = [[Xc + offs[c % 4] * dx, Yc + offs[c // 4] * dx] for c in range(16)]
+    ch = oracle.trace_points(P, xy)
+    assert img["I"][j, i] == pytest.approx(np.mean(ch["I_tot"]), rel=1e-15, abs=1e-300)
+    base_id = j * P.nx + i
+    mine = img["keys"][(img["keys"] >> np.uint64(16)) == base_id]
+    assert len(mine) == 16
+    assert set(int(k) & 0xFFFF for k in mine) == {(1 << 12) | (c << 8) for c in range(16)}
+
+
+def test_pixel_oracle_equals_image_oracle(oracle):
+    P = oracle.problem(metric=oracle.EINASTO, lam_E=0.1, chi=0.9, incl=math.radians(80.0),
+                       nx=12, ny=12, x_min=-12, x_max=12, y_min=-12, y_max=12, levels=2)
+    img = oracle.trace_image(P)
+    idx = np.argwhere(img["level"] > 0)
+    assert len(idx) > 0
+    for j, i in list(idx[:3]) + [(0, 0), (6, 6)]:
+        px = oracle.trace_pixel(P, int(i), int(j))
+        assert px["I"] == img["I"][j, i]
+        assert px["level"] == img["level"][j, i]
+        assert px["ncross"] == img["ncross"][j, i]
+        base_id = j * P.nx + i
+        mine = img["keys"][(img["keys"] >> np.uint64(16)) == base_id]
+        assert np.array_equal(np.sort(mine), px["keys"])
+
+
+def test_lensing_band_structure(oracle):
+    """Qualitative structure of Fig. 6: centre N_cross = 0 and captured,
+    surrounded by the direct (N = 1) and lensed (N = 2) domains."""
+    P = oracle.problem(chi=0.5, incl=math.radians(60.0), nx=24, ny=24)
+    img = oracle.trace_image(P)
+    assert img["status"][12, 12] == 1
+    assert (img["ncross"] == 1).sum() > 100
+    assert (img["ncross"] >= 2).sum() > 0
+    assert img["ncross"][0, 0] in (0, 1)
