@@ -1,0 +1,239 @@
+/*
+ * bhrt.h -- C ABI of the GB300 (sm_103a) ray tracer for rotating
+ * dark-matter-dressed black holes.
+ *
+ * The method (paper "Adaptive ray tracing, image diagnostics, and photon
+ * ring signatures of rotating dark-matter-dressed black holes"):
+ *   - rotating Kerr-like metric built from a static lapse H_i(R):
+ *     Kerr (H = 1 - 2/R), Einasto-type (Eq. 9), cored-NFW (Eq. 13), with
+ *     Sigma, F, Delta of Eqs. (23)-(25) and the Boyer-Lindquist components
+ *     of Eqs. (27)-(31);
+ *   - outer horizon R_+ = largest root of Delta (Eq. 33), extremal spin
+ *     Eqs. (34)-(37);
+ *   - backward null geodesics from a ZAMO screen (Sec. 3.2, Eqs. 63-74),
+ *     integrated as Hamilton's equations (Sec. 3.1, Eqs. 46-62);
+ *   - capture / escape (Eq. 75) and equatorial crossings (Sec. 3.3, 4.2)
+ *     with transfer maps R_em, phi_em, T_em (Eq. 82);
+ *   - redshift g (Eq. 89) for circular emitters (Eqs. 90-91) and the
+ *     semi-analytic emissivity (Eqs. 83-87), thin-disk intensity
+ *     sum over crossings of g^3 j (reading of Eq. 88);
+ *   - adaptive refinement of the screen near class boundaries
+ *     (Introduction and Sec. 4; the rule is a documented reading);
+ *   - image diagnostics (Sec. 6.2-6.3, Eqs. 92-107) and visibilities
+ *     (Sec. 6.4, Eqs. 108-109).
+ * Equation numbers are the paper's, counted in order of appearance.
+ *
+ * Conventions for every entry point:
+ *   - Units are dimensionless with M = 1 (Eq. 1).
+ *   - Struct arguments are HOST pointers.  Every array argument is a DEVICE
+ *     pointer owned by the caller unless stated otherwise.  The library
+ *     allocates no device memory of its own: scratch space is the caller's
+ *     workspace, sized by bh_workspace_size.
+ *   - Calls are asynchronous on the given stream (NULL = legacy default
+ *     stream).  Argument errors are returned synchronously before anything
+ *     is enqueued.  Errors detected on the device (queue overflow, time
+ *     budget) are written to a status word in the workspace and returned by
+ *     bh_workspace_status after the stream has been synchronised.
+ *   - The library never aborts and never prints.  Distinct streams with
+ *     distinct workspaces may be used concurrently from several threads.
+ *   - Screen: cell-centred grid X_i = x_min + (i + 1/2)(x_max - x_min)/nx,
+ *     Y_j = y_min + (j + 1/2)(y_max - y_min)/ny; planes are row-major
+ *     [ny][nx] with j the row (Y) index.  X is the horizontal celestial
+ *     coordinate in the sign convention of Eq. (72).
+ */
+#ifndef BHRT_H
+#define BHRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BH_KERR = 0,    /* H = 1 - 2/R (Kerr reference, Sec. 2.2)              */
+  BH_EINASTO = 1, /* Einasto-type regular black hole, Eq. (9)             */
+  BH_CNFW = 2     /* cored-NFW black hole, Eq. (13)                       */
+} bh_metric;
+
+typedef enum {
+  BH_OK = 0,
+  BH_ERR_INVALID_ARG = 1,     /* NULL pointer, size or parameter out of range */
+  BH_ERR_NO_HORIZON = 2,      /* Delta has no root: |chi| > chi_e (Eqs. 33-37) */
+  BH_ERR_OBSERVER_INSIDE = 3, /* R_o <= 10 R_+, or R_o inside the escape test  */
+  BH_ERR_WORKSPACE = 4,       /* workspace missing, misaligned or too small    */
+  BH_ERR_CUDA = 5,            /* a CUDA runtime call failed                    */
+  BH_ERR_TIMEOUT = 6,         /* device time budget exceeded (integrator)      */
+  BH_ERR_QUEUE_OVERFLOW = 7,  /* refinement list capacity exceeded             */
+  BH_ERR_NO_ISCO = 8          /* no stable circular orbit found for R_in       */
+} bh_status;
+
+/* Spacetime: metric family and halo parameters (Sec. 2.1, Eqs. 9-14). */
+typedef struct {
+  int32_t metric;   /* bh_metric */
+  int32_t reserved; /* must be 0 */
+  double chi;       /* spin a/M (Eq. 1); |chi| below the extremal spin */
+  double lambda_E;  /* Einasto scale l_E/M (Eq. 10), > 0, used by BH_EINASTO */
+  double eta;       /* cored-NFW 4 pi rho_0 r_0^2 (Eq. 14), >= 0, BH_CNFW   */
+  double lambda_c;  /* cored-NFW core radius r_0/M (Eq. 12), > 0, BH_CNFW   */
+} bh_spacetime;
+
+/* Observer and screen (Sec. 3.2 and Sec. 4). */
+typedef struct {
+  double r_obs;            /* observer radius R_o (> 10 R_+)              */
+  double incl;             /* inclination theta_o in radians, (0, pi)      */
+  double x_min, x_max;     /* screen extent in X                           */
+  double y_min, y_max;     /* screen extent in Y                           */
+  int32_t nx, ny;          /* base resolution, 1 .. 16384 each             */
+  int32_t refine_levels;   /* adaptive 4x4 refinement depth, 0 .. 3        */
+  int32_t reserved;        /* must be 0                                    */
+  int64_t refine_capacity; /* max cells per refinement level per call;
+                              0 selects max(16 * nx * ny * n_images, 65536) */
+} bh_camera;
+
+/* Emission (Sec. 5.1, Eqs. 83-87).  The thin-disk path evaluates j on the
+ * equatorial plane (z = 0), so H0 and h only matter for off-plane use. */
+typedef struct {
+  int32_t r_in_mode;  /* 0: R_in = r_ISCO (prograde); 1: R_in = R_+ + dR_in (Eq. 87) */
+  int32_t reserved;   /* must be 0 */
+  double j0, p, R_s;  /* normalisation, radial power, radial scale (Eq. 83) */
+  double sigma_in, sigma_out, R_out; /* tapers, Eqs. (85)-(86)             */
+  double dR_in;       /* used when r_in_mode == 1                           */
+  double H0, h;       /* disk height H(rho) = H0 + h rho, Eq. (84)          */
+} bh_emission;
+
+/* Integrator (the paper names none; these are the build's readings). */
+typedef struct {
+  int32_t precision;    /* 0: all-FP64; 1: mixed (FP32 bulk, FP64 promoted) */
+  int32_t max_steps;    /* attempted steps per ray before status 2          */
+  double rtol, atol;    /* Dormand-Prince 5(4) tolerances                   */
+  double cap_factor;    /* capture when R < cap_factor * R_+ (Eq. 75)       */
+  double esc_factor;    /* escape when R > esc_factor * R_o                 */
+  double thetadot_min;  /* trusted crossing needs |dtheta/dlambda| >= this  */
+  double dlambda_min;   /* and an affine gap >= this to the previous one    */
+  double promote_dr;    /* mixed: FP64 steps while R < R_+ + promote_dr     */
+  double time_budget_s; /* device time budget per call (s); 0 = none      */
+} bh_integrator;
+
+/* Per-pixel output planes (device pointers, caller-owned).  Any pointer
+ * marked optional may be NULL. */
+typedef struct {
+  float* I;               /* [ny*nx] total intensity, leaf mean             */
+  float* I_n;             /* optional [3][ny*nx] orders n = 0, 1, 2         */
+  uint8_t* ncross;        /* [ny*nx] trusted crossings of the base ray (<=255) */
+  uint8_t* status;        /* [ny*nx] 0 escaped, 1 captured, 2 undetermined  */
+  uint8_t* refine_level;  /* optional [ny*nx] deepest refinement level      */
+  float* R_em;            /* optional [3][ny*nx] transfer maps of the base  */
+  float* phi_em;          /*   ray's crossings n = 0, 1, 2 (Eq. 82); 0 where */
+  float* T_em;            /*   the crossing does not exist                  */
+  float* g;               /* optional [3][ny*nx] redshift factor (Eq. 89)   */
+  float* h_drift;         /* optional [ny*nx] max |2 Sigma H| Delta / P^2   */
+  uint64_t* refine_keys;  /* optional list of traced refined cells:
+                             base_id << 16 | level << 12 | d1 << 8 | d2 << 4 | d3,
+                             d_l = 4*row + col of the 4x4 child at level l */
+  int64_t refine_keys_cap;   /* capacity of refine_keys                      */
+  int64_t* refine_keys_count; /* optional device int64: number of keys (may
+                                 exceed the capacity, then the list is cut) */
+} bh_image_out;
+
+/* Per-ray record returned by bh_trace_points (device array of structs). */
+typedef struct {
+  int32_t status, ncross;
+  int32_t n_accept, n_reject;
+  double I_tot, I_n[3];
+  double R_em[3], phi_em[3], T_em[3], g[3];
+  double E, ell, h_drift, lambda_end;
+} bh_ray_record;
+
+/* ---------------------------------------------------------------------- */
+
+/* Host-side geometry of one spacetime: r_plus = R_+ (Eq. 33), chi_e
+ * (Eqs. 36-37, computed with chi ignored), r_isco (prograde circular-orbit
+ * energy minimum, from Eqs. 90-91).  Any output may be NULL.
+ * Returns BH_ERR_NO_HORIZON (r_plus, r_isco untouched) if |chi| >= chi_e. */
+bh_status bh_host_geometry(const bh_spacetime* st, double* r_plus, double* chi_e,
+                           double* r_isco);
+
+/* Bytes of device workspace needed by bh_trace_batch with n images of the
+ * given cameras (all n cameras must share nx, ny and refine_levels) and
+ * integrator precision (integ may be NULL: FP64).  The mixed path needs two
+ * hand-off queues on top of the refinement lists.  The workspace must be
+ * 256-byte aligned. */
+bh_status bh_workspace_size(int32_t n, const bh_camera* cameras, const bh_integrator* integ,
+                            size_t* bytes);
+
+/* Traces one image: per-pixel backward geodesics, crossings, g, intensity,
+ * refinement and assembly.  Equivalent to bh_trace_batch with n = 1. */
+bh_status bh_trace_image(const bh_spacetime* st, const bh_camera* cam, const bh_emission* em,
+                         const bh_integrator* integ, const bh_image_out* out, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/* Traces n images in one persistent work-queue launch per refinement level.
+ * st, cam, em, integ, out are host arrays of n structs; all cameras share
+ * nx, ny, refine_levels and all integrators share precision.  Images may mix
+ * metric families and parameters. */
+bh_status bh_trace_batch(int32_t n, const bh_spacetime* st, const bh_camera* cam,
+                         const bh_emission* em, const bh_integrator* integ,
+                         const bh_image_out* out, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Traces single rays from explicit screen points xy[2*k], xy[2*k+1]
+ * (device doubles) into records[k] (device).  Same physics as the image
+ * path, no refinement.  Needs bh_points_workspace_size(n) bytes. */
+bh_status bh_points_workspace_size(int64_t n, size_t* bytes);
+bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh_emission* em,
+                          const bh_integrator* integ, int64_t n, const double* xy,
+                          bh_ray_record* records, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Plans: a batch whose per-image constants are computed and uploaded once,
+ * then launched any number of times.  bh_plan_launch with use_graph != 0
+ * captures the whole launch sequence (persistent trace launch per level,
+ * refinement, assembly) into a CUDA graph on first use and replays it
+ * afterwards; the stream must then be a non-legacy stream and the output
+ * and workspace pointers given at creation must stay valid.  A plan owns
+ * host memory only.  Outputs and workspace follow bh_trace_batch. */
+typedef struct bh_plan_s* bh_plan;
+
+typedef struct {
+  int64_t cells[4];        /* cells per level (level 0 = n * nx * ny)         */
+  int64_t rays[4];         /* rays integrated to termination per level        */
+  int64_t accepted_fp64;   /* accepted Dormand-Prince steps taken in FP64     */
+  int64_t rejected_fp64;   /* rejected FP64 trial steps                       */
+  int64_t accepted_fp32;   /* mixed precision: accepted FP32 steps            */
+  int64_t rejected_fp32;   /* mixed precision: rejected FP32 trial steps      */
+  int64_t promoted_rays;   /* mixed precision: rays handed to the FP64 pass   */
+  int64_t spill_full;      /* promotions refused because the queue was full   */
+  double trace_ms[4];      /* per-level trace time (all passes) of the last
+                              launch when timing is on, else -1               */
+  double fp32_ms, fp64_ms; /* trace kernel time by precision (timing on)      */
+  int32_t kernel_launches; /* kernels enqueued per launch                     */
+  int32_t status;          /* device status word (bh_status)                  */
+  int32_t trace_blocks, trace_threads; /* trace launch shape in use           */
+} bh_run_stats;
+
+/* Validates, computes per-image constants and uploads them to the
+ * workspace (synchronises the stream once). */
+bh_status bh_plan_create(int32_t n, const bh_spacetime* st, const bh_camera* cam,
+                         const bh_emission* em, const bh_integrator* integ,
+                         const bh_image_out* out, void* workspace, size_t workspace_bytes,
+                         void* stream, bh_plan* plan);
+bh_status bh_plan_launch(bh_plan plan, int32_t use_graph, void* stream);
+/* Records CUDA events around each trace launch (disables graph replay). */
+bh_status bh_plan_set_timing(bh_plan plan, int32_t enable);
+/* Counters of the last launch (blocking copy on `stream`). */
+bh_status bh_plan_stats(bh_plan plan, void* stream, bh_run_stats* out);
+bh_status bh_plan_destroy(bh_plan plan);
+
+/* Device status word of the last call that used this workspace (blocking
+ * copy; call after synchronising the stream). */
+bh_status bh_workspace_status(const void* workspace, void* stream);
+
+const char* bh_status_string(bh_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BHRT_H */

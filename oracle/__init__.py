@@ -126,6 +126,9 @@ def _load():
                                         C.POINTER(C.c_int64)]
         lib.orc_trace_pixel.restype = C.c_int
         lib.orc_geometry.argtypes = [P, D]; lib.orc_geometry.restype = C.c_int
+        lib.orc_trace_pixels.argtypes = [P, C.c_int64, C.POINTER(C.c_int32), D,
+                                         C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+        lib.orc_trace_pixels.restype = C.c_int
         _lib = lib
         return lib
 
@@ -337,3 +340,19 @@ def trace_pixel(P: Problem, i: int, j: int, keys_cap: int = 1 << 16) -> dict:
     return dict(I=val[0], I_n=val[1:].copy(), level=lev.value, status=ray.status,
                 ncross=ray.ncross, R_em=np.array(ray.R_em), g=np.array(ray.g),
                 keys=np.sort(keys[: cnt.value]), ray=ray)
+
+
+def trace_pixels(P: Problem, ij) -> dict:
+    """Many base pixels with their refinement subtrees (parallel over pixels).
+    Returns per-pixel values, deepest levels and the rays each one cost."""
+    ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int32).reshape(-1, 2))
+    n = ij.shape[0]
+    val = np.zeros((max(n, 1), 4))
+    lev = np.zeros(max(n, 1), np.int32)
+    nr = np.zeros(max(n, 1), np.int64)
+    rc = _load().orc_trace_pixels(C.byref(P), n, ij.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  _dp(val), lev.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  nr.ctypes.data_as(C.POINTER(C.c_int64)))
+    if rc:
+        raise ValueError(f"oracle trace_pixels failed (code {rc})")
+    return dict(val=val[:n], level=lev[:n], rays=nr[:n])

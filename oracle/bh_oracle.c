@@ -588,13 +588,14 @@ static void orc_geo_rhs(void* c, const double* y, double* dy) {
   orc_rhs(g->P, g->E, g->ell, y, dy);
 }
 
-/* A stage is admissible only outside the horizon (Delta > 0) and with
- * 0 < theta < pi; otherwise the trial step is rejected and halved. */
+/* A stage is admissible only outside the horizon (Delta > 0); otherwise
+ * the trial step is rejected and halved.  theta may leave (0, pi) inside a
+ * step: the equations continue smoothly through the polar axis, and the
+ * accepted state is reflected back (reading; see orc_trace_ray). */
 static int orc_geo_valid(void* c, const double* y) {
   orc_geo_ctx* g = (orc_geo_ctx*)c;
   if (!(y[1] > 0.0) || !isfinite(y[1])) return 0;
   if (!(orc_Delta(g->P, y[1]) > 0.0)) return 0;
-  if (!(y[2] > 0.0 && y[2] < M_PI)) return 0;
   for (int i = 0; i < 6; ++i) if (!isfinite(y[i])) return 0;
   return 1;
 }
@@ -708,6 +709,15 @@ int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y,
     }
     lam += h;
     for (int i = 0; i < 6; ++i) { y[i] = y1[i]; k[0][i] = k[6][i]; }
+    /* Polar axis (reading): a ray that passed through theta = 0 or pi is
+     * mapped back to (0, pi) by (theta, p_theta, phi) -> (-theta, -p_theta,
+     * phi + pi) or (2 pi - theta, -p_theta, phi + pi). */
+    if (y[2] < 0.0 || y[2] > M_PI) {
+      y[2] = (y[2] < 0.0) ? -y[2] : 2.0 * M_PI - y[2];
+      y[5] = -y[5];
+      y[3] += M_PI;
+      orc_geo_rhs(&ctx, y, k[0]);
+    }
     /* Null-constraint monitor (Sec. 3.1, after Eq. 62), scaled by the
      * dominant radial term P^2/(Delta Sigma). */
     {
@@ -915,6 +925,30 @@ int orc_trace_pixel(const orc_problem* P, int i, int j, orc_ray* base_ray, doubl
     *level = orc_refine_cell(P, &G, X, Y, dx, dy, 0,
                              (uint64_t)((int64_t)j * nx + i) << 16, &K, val);
   *count = K.count;
+  return 0;
+}
+
+/* Many base pixels, each with its refinement subtree (OpenMP over pixels).
+ * ij[2k] = i, ij[2k+1] = j.  val4[4k..4k+3] = (I_tot, I_0, I_1, I_2),
+ * level[k] = deepest level, nrays[k] = rays integrated for pixel k
+ * (its own ray, its on-screen neighbours and its subtree).  Used to time the
+ * oracle on a bounded sample of a workload. */
+int orc_trace_pixels(const orc_problem* P, int64_t n, const int32_t* ij, double* val4,
+                     int32_t* level, int64_t* nrays) {
+  orc_geom G;
+  int rc = orc_geometry_setup(P, &G);
+  if (rc) return rc;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < n; ++k) {
+    orc_ray r;
+    uint64_t keys[4096 + 256];
+    int64_t cnt = 0;
+    orc_trace_pixel(P, ij[2 * k], ij[2 * k + 1], &r, val4 + 4 * k, &level[k], keys, 4096 + 256,
+                    &cnt);
+    int i = ij[2 * k], j = ij[2 * k + 1], nb = 0;
+    if (P->levels > 0) nb = (i > 0) + (i + 1 < P->nx) + (j > 0) + (j + 1 < P->ny);
+    nrays[k] = 1 + nb + cnt;
+  }
   return 0;
 }
 

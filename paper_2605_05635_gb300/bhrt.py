@@ -1,0 +1,411 @@
+"""Thin ctypes binding of ``libbhrt.so`` (C ABI declared in include/bhrt.h).
+
+The binding only marshals arguments: it allocates outputs and the workspace
+as torch CUDA tensors and passes raw device pointers and the current CUDA
+stream to the library.  Every step of the computation runs in the library's
+kernels; there is no CPU or PyTorch fallback, and a missing or unloadable
+library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+import os
+import threading
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+from . import _build
+
+KERR, EINASTO, CNFW = 0, 1, 2
+FP64, MIXED = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BHRTError(RuntimeError):
+    """A bh_status other than BH_OK."""
+
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (bh_status {code})")
+
+
+# --------------------------------------------------------------- ABI structs
+class _Spacetime(C.Structure):
+    _fields_ = [("metric", C.c_int32), ("reserved", C.c_int32), ("chi", C.c_double),
+                ("lambda_E", C.c_double), ("eta", C.c_double), ("lambda_c", C.c_double)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("r_obs", C.c_double), ("incl", C.c_double), ("x_min", C.c_double),
+                ("x_max", C.c_double), ("y_min", C.c_double), ("y_max", C.c_double),
+                ("nx", C.c_int32), ("ny", C.c_int32), ("refine_levels", C.c_int32),
+                ("reserved", C.c_int32), ("refine_capacity", C.c_int64)]
+
+
+class _Emission(C.Structure):
+    _fields_ = [("r_in_mode", C.c_int32), ("reserved", C.c_int32), ("j0", C.c_double),
+                ("p", C.c_double), ("R_s", C.c_double), ("sigma_in", C.c_double),
+                ("sigma_out", C.c_double), ("R_out", C.c_double), ("dR_in", C.c_double),
+                ("H0", C.c_double), ("h", C.c_double)]
+
+
+class _Integrator(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_steps", C.c_int32), ("rtol", C.c_double),
+                ("atol", C.c_double), ("cap_factor", C.c_double), ("esc_factor", C.c_double),
+                ("thetadot_min", C.c_double), ("dlambda_min", C.c_double),
+                ("promote_dr", C.c_double), ("time_budget_s", C.c_double)]
+
+
+class _ImageOut(C.Structure):
+    _fields_ = [("I", C.c_void_p), ("I_n", C.c_void_p), ("ncross", C.c_void_p),
+                ("status", C.c_void_p), ("refine_level", C.c_void_p), ("R_em", C.c_void_p),
+                ("phi_em", C.c_void_p), ("T_em", C.c_void_p), ("g", C.c_void_p),
+                ("h_drift", C.c_void_p), ("refine_keys", C.c_void_p),
+                ("refine_keys_cap", C.c_int64), ("refine_keys_count", C.c_void_p)]
+
+
+class RayRecord(C.Structure):
+    _fields_ = [("status", C.c_int32), ("ncross", C.c_int32), ("n_accept", C.c_int32),
+                ("n_reject", C.c_int32), ("I_tot", C.c_double), ("I_n", C.c_double * 3),
+                ("R_em", C.c_double * 3), ("phi_em", C.c_double * 3),
+                ("T_em", C.c_double * 3), ("g", C.c_double * 3), ("E", C.c_double),
+                ("ell", C.c_double), ("h_drift", C.c_double), ("lambda_end", C.c_double)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("cells", C.c_int64 * 4), ("rays", C.c_int64 * 4),
+                ("accepted_fp64", C.c_int64), ("rejected_fp64", C.c_int64),
+                ("accepted_fp32", C.c_int64), ("rejected_fp32", C.c_int64),
+                ("promoted_rays", C.c_int64), ("spill_full", C.c_int64),
+                ("trace_ms", C.c_double * 4), ("fp32_ms", C.c_double), ("fp64_ms", C.c_double),
+                ("kernel_launches", C.c_int32), ("status", C.c_int32),
+                ("trace_blocks", C.c_int32), ("trace_threads", C.c_int32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        for k in ("cells", "rays", "trace_ms"):
+            d[k] = list(d[k])
+        return d
+
+
+# ----------------------------------------------------------- user parameters
+@dataclasses.dataclass
+class Spacetime:
+    metric: int = KERR
+    chi: float = 0.5
+    lambda_E: float = 0.1
+    eta: float = 0.02
+    lambda_c: float = 10.0
+
+    def _c(self):
+        return _Spacetime(self.metric, 0, self.chi, self.lambda_E, self.eta, self.lambda_c)
+
+
+@dataclasses.dataclass
+class Camera:
+    r_obs: float = 1000.0
+    incl: float = math.radians(17.0)
+    x_min: float = -10.0
+    x_max: float = 10.0
+    y_min: float = -10.0
+    y_max: float = 10.0
+    nx: int = 64
+    ny: int = 64
+    refine_levels: int = 0
+    refine_capacity: int = 0
+
+    def _c(self):
+        return _Camera(self.r_obs, self.incl, self.x_min, self.x_max, self.y_min, self.y_max,
+                       self.nx, self.ny, self.refine_levels, 0, self.refine_capacity)
+
+
+@dataclasses.dataclass
+class Emission:
+    r_in_mode: int = 0
+    j0: float = 1.0
+    p: float = 2.0
+    R_s: float = 8.0
+    sigma_in: float = 0.2
+    sigma_out: float = 2.0
+    R_out: float = 20.0
+    dR_in: float = 0.5
+    H0: float = 0.05
+    h: float = 0.05
+
+    def _c(self):
+        return _Emission(self.r_in_mode, 0, self.j0, self.p, self.R_s, self.sigma_in,
+                         self.sigma_out, self.R_out, self.dR_in, self.H0, self.h)
+
+
+@dataclasses.dataclass
+class Integrator:
+    precision: int = FP64
+    max_steps: int = 1_000_000
+    rtol: float = 1e-10
+    atol: float = 1e-12
+    cap_factor: float = 1.01
+    esc_factor: float = 1.1
+    thetadot_min: float = 1e-8
+    dlambda_min: float = 1e-6
+    promote_dr: float = 0.1
+    time_budget_s: float = 0.0
+
+    def _c(self):
+        return _Integrator(self.precision, self.max_steps, self.rtol, self.atol,
+                           self.cap_factor, self.esc_factor, self.thetadot_min,
+                           self.dlambda_min, self.promote_dr, self.time_budget_s)
+
+
+def from_flat(d: dict):
+    """Split a flat parameter dict (oracle naming) into the four structs."""
+    st = Spacetime(metric=d.get("metric", KERR), chi=d.get("chi", 0.5),
+                   lambda_E=d.get("lam_E", 0.1), eta=d.get("eta", 0.02),
+                   lambda_c=d.get("lam_c", 10.0))
+    cam = Camera(r_obs=d.get("r_obs", 1000.0), incl=d.get("incl", math.radians(17.0)),
+                 x_min=d.get("x_min", -10.0), x_max=d.get("x_max", 10.0),
+                 y_min=d.get("y_min", -10.0), y_max=d.get("y_max", 10.0),
+                 nx=d.get("nx", 64), ny=d.get("ny", 64), refine_levels=d.get("levels", 0),
+                 refine_capacity=d.get("refine_capacity", 0))
+    em = Emission(r_in_mode=d.get("r_in_mode", 0), j0=d.get("j0", 1.0), p=d.get("p", 2.0),
+                  R_s=d.get("R_s", 8.0), sigma_in=d.get("sigma_in", 0.2),
+                  sigma_out=d.get("sigma_out", 2.0), R_out=d.get("R_out", 20.0),
+                  dR_in=d.get("dR_in", 0.5), H0=d.get("H0", 0.05), h=d.get("h", 0.05))
+    it = Integrator(precision=d.get("precision", FP64), max_steps=d.get("max_steps", 1_000_000),
+                    rtol=d.get("rtol", 1e-10), atol=d.get("atol", 1e-12),
+                    cap_factor=d.get("cap_factor", 1.01), esc_factor=d.get("esc_factor", 1.1),
+                    thetadot_min=d.get("thetadot_min", 1e-8),
+                    dlambda_min=d.get("dlambda_min", 1e-6),
+                    promote_dr=d.get("promote_dr", 0.1),
+                    time_budget_s=d.get("time_budget_s", 0.0))
+    return st, cam, em, it
+
+
+# ------------------------------------------------------------------ library
+def lib():
+    """Load (building first if needed) the CUDA library; raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not _build.up_to_date():
+            _build.build()
+        L = C.CDLL(path)
+        P = C.POINTER
+        L.bh_status_string.argtypes = [C.c_int]
+        L.bh_status_string.restype = C.c_char_p
+        L.bh_host_geometry.argtypes = [P(_Spacetime), P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.bh_workspace_size.argtypes = [C.c_int32, P(_Camera), P(_Integrator), P(C.c_size_t)]
+        L.bh_trace_image.argtypes = [P(_Spacetime), P(_Camera), P(_Emission), P(_Integrator),
+                                     P(_ImageOut), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.bh_trace_batch.argtypes = [C.c_int32, P(_Spacetime), P(_Camera), P(_Emission),
+                                     P(_Integrator), P(_ImageOut), C.c_void_p, C.c_size_t,
+                                     C.c_void_p]
+        L.bh_points_workspace_size.argtypes = [C.c_int64, P(C.c_size_t)]
+        L.bh_trace_points.argtypes = [P(_Spacetime), P(_Camera), P(_Emission), P(_Integrator),
+                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                      C.c_void_p]
+        L.bh_workspace_status.argtypes = [C.c_void_p, C.c_void_p]
+        L.bh_plan_create.argtypes = [C.c_int32, P(_Spacetime), P(_Camera), P(_Emission),
+                                     P(_Integrator), P(_ImageOut), C.c_void_p, C.c_size_t,
+                                     C.c_void_p, P(C.c_void_p)]
+        L.bh_plan_launch.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+        L.bh_plan_set_timing.argtypes = [C.c_void_p, C.c_int32]
+        L.bh_plan_stats.argtypes = [C.c_void_p, C.c_void_p, P(RunStats)]
+        L.bh_plan_destroy.argtypes = [C.c_void_p]
+        for fn in ("bh_host_geometry", "bh_workspace_size", "bh_trace_image", "bh_trace_batch",
+                   "bh_points_workspace_size", "bh_trace_points", "bh_workspace_status",
+                   "bh_plan_create", "bh_plan_launch", "bh_plan_set_timing", "bh_plan_stats",
+                   "bh_plan_destroy"):
+            getattr(L, fn).restype = C.c_int
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    return lib().bh_status_string(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise BHRTError(code, where)
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(device):
+    if not torch.cuda.is_available():
+        raise RuntimeError("bhrt needs a CUDA device; there is no CPU fallback")
+    return torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+
+
+def host_geometry(st: Spacetime):
+    """(r_plus, chi_e, r_isco) from the library's host geometry."""
+    rp, ce, ri = C.c_double(0), C.c_double(0), C.c_double(0)
+    code = lib().bh_host_geometry(C.byref(st._c()), C.byref(rp), C.byref(ce), C.byref(ri))
+    _check(code, "bh_host_geometry")
+    return rp.value, ce.value, ri.value
+
+
+def _aligned_workspace(nbytes: int, device) -> torch.Tensor:
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + nbytes]
+
+
+def workspace_bytes(cams: Sequence[Camera], integ: Optional[Integrator] = None) -> int:
+    arr = (_Camera * len(cams))(*[c._c() for c in cams])
+    n = C.c_size_t(0)
+    it = C.byref(integ._c()) if integ is not None else None
+    _check(lib().bh_workspace_size(len(cams), arr, it, C.byref(n)), "bh_workspace_size")
+    return n.value
+
+
+def alloc_outputs(cam: Camera, device, keys_cap: int = 0) -> Dict[str, torch.Tensor]:
+    ny, nx = cam.ny, cam.nx
+    f = dict(dtype=torch.float32, device=device)
+    u8 = dict(dtype=torch.uint8, device=device)
+    out = dict(I=torch.empty(ny, nx, **f), I_n=torch.empty(3, ny, nx, **f),
+               ncross=torch.empty(ny, nx, **u8), status=torch.empty(ny, nx, **u8),
+               refine_level=torch.empty(ny, nx, **u8), R_em=torch.empty(3, ny, nx, **f),
+               phi_em=torch.empty(3, ny, nx, **f), T_em=torch.empty(3, ny, nx, **f),
+               g=torch.empty(3, ny, nx, **f), h_drift=torch.empty(ny, nx, **f))
+    if keys_cap:
+        out["refine_keys"] = torch.empty(keys_cap, dtype=torch.int64, device=device)
+        out["refine_keys_count"] = torch.zeros(1, dtype=torch.int64, device=device)
+    return out
+
+
+def _image_out(o: Dict[str, torch.Tensor]) -> _ImageOut:
+    def ptr(k):
+        t = o.get(k)
+        return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+    keys = o.get("refine_keys")
+    return _ImageOut(ptr("I"), ptr("I_n"), ptr("ncross"), ptr("status"), ptr("refine_level"),
+                     ptr("R_em"), ptr("phi_em"), ptr("T_em"), ptr("g"), ptr("h_drift"),
+                     ptr("refine_keys"), keys.numel() if keys is not None else 0,
+                     ptr("refine_keys_count"))
+
+
+def trace_batch(items: Sequence[tuple], device=None, stream=None, keys_cap: int = 0,
+                outputs: Optional[List[Dict[str, torch.Tensor]]] = None,
+                workspace: Optional[torch.Tensor] = None, check: bool = True):
+    """Trace several images in one call.  ``items`` is a sequence of
+    (Spacetime, Camera, Emission, Integrator) tuples.  Returns the list of
+    output dicts (torch tensors on the device)."""
+    device = _need_cuda(device)
+    n = len(items)
+    sts = (_Spacetime * n)(*[it[0]._c() for it in items])
+    cams = (_Camera * n)(*[it[1]._c() for it in items])
+    ems = (_Emission * n)(*[it[2]._c() for it in items])
+    ints = (_Integrator * n)(*[it[3]._c() for it in items])
+    if outputs is None:
+        outputs = [alloc_outputs(it[1], device, keys_cap) for it in items]
+    outs = (_ImageOut * n)(*[_image_out(o) for o in outputs])
+    nbytes = workspace_bytes([it[1] for it in items], items[0][3])
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = _aligned_workspace(nbytes, device)
+    sp = _stream_ptr(stream)
+    code = lib().bh_trace_batch(n, sts, cams, ems, ints, outs, C.c_void_p(workspace.data_ptr()),
+                                workspace.numel(), sp)
+    _check(code, "bh_trace_batch")
+    if check:
+        _check(lib().bh_workspace_status(C.c_void_p(workspace.data_ptr()), sp), "device status")
+        for o in outputs:
+            if "refine_keys_count" in o:
+                cnt = int(o["refine_keys_count"].item())
+                o["refine_keys"] = o["refine_keys"][:min(cnt, o["refine_keys"].numel())]
+    return outputs
+
+
+def trace_image(st: Spacetime, cam: Camera, em: Emission, integ: Integrator, device=None,
+                stream=None, keys_cap: int = 0, check: bool = True):
+    return trace_batch([(st, cam, em, integ)], device=device, stream=stream, keys_cap=keys_cap,
+                       check=check)[0]
+
+
+def trace_points(st: Spacetime, cam: Camera, em: Emission, integ: Integrator, xy, device=None,
+                 stream=None):
+    """Trace rays from explicit screen points ``xy`` (N x 2); returns a numpy
+    structured array of ray records."""
+    import numpy as np
+
+    device = _need_cuda(device)
+    xy_t = torch.as_tensor(xy, dtype=torch.float64).reshape(-1, 2).contiguous().to(device)
+    n = xy_t.shape[0]
+    rec = torch.empty(max(n, 1) * C.sizeof(RayRecord), dtype=torch.uint8, device=device)
+    nb = C.c_size_t(0)
+    _check(lib().bh_points_workspace_size(n, C.byref(nb)), "bh_points_workspace_size")
+    ws = _aligned_workspace(nb.value, device)
+    sp = _stream_ptr(stream)
+    code = lib().bh_trace_points(C.byref(st._c()), C.byref(cam._c()), C.byref(em._c()),
+                                 C.byref(integ._c()), n, C.c_void_p(xy_t.data_ptr()),
+                                 C.c_void_p(rec.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                 ws.numel(), sp)
+    _check(code, "bh_trace_points")
+    _check(lib().bh_workspace_status(C.c_void_p(ws.data_ptr()), sp), "device status")
+    raw = rec[: n * C.sizeof(RayRecord)].cpu().numpy().tobytes()
+    dt = np.dtype([(f, np.int32) if t is C.c_int32 else
+                   ((f, np.float64, (3,)) if hasattr(t, "_length_") else (f, np.float64))
+                   for f, t in RayRecord._fields_])
+    return np.frombuffer(raw, dtype=dt, count=n).copy()
+
+
+class Plan:
+    """A batch whose constants are uploaded once and that is launched many
+    times (optionally as a CUDA graph replay).  Outputs and workspace are
+    torch tensors owned by the plan object."""
+
+    def __init__(self, items: Sequence[tuple], device=None, stream=None, keys_cap: int = 0):
+        self.device = _need_cuda(device)
+        self.items = list(items)
+        n = len(self.items)
+        self.outputs = [alloc_outputs(it[1], self.device, keys_cap) for it in self.items]
+        sts = (_Spacetime * n)(*[it[0]._c() for it in self.items])
+        cams = (_Camera * n)(*[it[1]._c() for it in self.items])
+        ems = (_Emission * n)(*[it[2]._c() for it in self.items])
+        ints = (_Integrator * n)(*[it[3]._c() for it in self.items])
+        outs = (_ImageOut * n)(*[_image_out(o) for o in self.outputs])
+        nbytes = workspace_bytes([it[1] for it in self.items], self.items[0][3])
+        self.workspace = _aligned_workspace(nbytes, self.device)
+        self._h = C.c_void_p(0)
+        code = lib().bh_plan_create(n, sts, cams, ems, ints, outs,
+                                    C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                                    _stream_ptr(stream), C.byref(self._h))
+        _check(code, "bh_plan_create")
+
+    def launch(self, use_graph: bool = False, stream=None):
+        _check(lib().bh_plan_launch(self._h, int(use_graph), _stream_ptr(stream)),
+               "bh_plan_launch")
+
+    def set_timing(self, enable: bool):
+        _check(lib().bh_plan_set_timing(self._h, int(enable)), "bh_plan_set_timing")
+
+    def stats(self, stream=None) -> dict:
+        st = RunStats()
+        _check(lib().bh_plan_stats(self._h, _stream_ptr(stream), C.byref(st)), "bh_plan_stats")
+        return st.as_dict()
+
+    def check(self, stream=None):
+        _check(lib().bh_workspace_status(C.c_void_p(self.workspace.data_ptr()),
+                                         _stream_ptr(stream)), "device status")
+
+    def close(self):
+        if self._h:
+            lib().bh_plan_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,531 @@
+// integrator.cuh -- device pieces shared by the FP64 and the mixed-precision
+// trace kernels: Dormand-Prince 5(4) tableau and dense output, the launch
+// from the ZAMO screen, the FP64 step with crossing events, the emitter
+// redshift and emissivity, the hand-off records between precision passes and
+// the terminal write of a ray's results.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace bhrt {
+
+// Dormand & Prince (1980) RK5(4)7M tableau, FSAL; 4th-order continuous
+// extension (Shampine 1986; Hairer, Norsett & Wanner, Solving ODEs I).
+struct DPTab {
+  double a[7][6];
+  double b[7];
+  double e[7];  // b - b*
+  double d[7];  // dense-output correction
+};
+__device__ constexpr DPTab kDP = {
+    {{0, 0, 0, 0, 0, 0},
+     {1.0 / 5, 0, 0, 0, 0, 0},
+     {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+     {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+     {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+     {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+     {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0},
+    {35.0 / 384 - 5179.0 / 57600, 0, 500.0 / 1113 - 7571.0 / 16695, 125.0 / 192 - 393.0 / 640,
+     -2187.0 / 6784 + 92097.0 / 339200, 11.0 / 84 - 187.0 / 2100, -1.0 / 40},
+    {-12715105075.0 / 11282082432.0, 0, 87487479700.0 / 32700410799.0,
+     -10690763975.0 / 1880347072.0, 701980252875.0 / 199316789632.0,
+     -1453857185.0 / 822651844.0, 69997945.0 / 29380423.0}};
+
+constexpr double kHalfPi = 1.57079632679489661923;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Step-size factor: safety 0.9, clamp [0.2, 10], no growth right after a
+// rejection; err^(-1/5) evaluated in FP32 (it only steers the step size).
+__device__ __forceinline__ float step_factor(float e, bool after_reject) {
+  float fac = (e == 0.f) ? 10.f : 0.9f * exp2f(-0.2f * log2f(e));
+  return fminf(fmaxf(fac, 0.2f), after_reject ? 1.f : 10.f);
+}
+
+// Dense output of one component: y(x0 + sig h).
+__device__ __forceinline__ double dense1(double y0, double y1, double hf0, double hf1, double hd,
+                                         double sig) {
+  double r2 = y1 - y0;
+  double r3 = hf0 - r2;
+  double r4 = r2 - hf1 - r3;
+  return y0 + sig * (r2 + (1.0 - sig) * (r3 + sig * (r4 + (1.0 - sig) * hd)));
+}
+
+template <class T>
+__device__ __forceinline__ MetricConsts<T> metric_consts(const ImgParams& ip) {
+  MetricConsts<T> m;
+  m.metric = ip.metric;
+  m.chi = (T)ip.chi;
+  m.chi2 = (T)(ip.chi * ip.chi);
+  m.il = ip.metric == 1 ? (T)(1.0 / ip.lamE) : T(0);
+  m.lc = (T)ip.lamc;
+  m.ilc = ip.metric == 2 ? (T)(1.0 / ip.lamc) : T(0);
+  m.eta_lc = (T)(ip.eta * ip.lamc);
+  return m;
+}
+
+// Circular equatorial emitter at R (Eqs. 90-91 at theta = pi/2, where
+// d_R g_TT = -H', d_R g_Tphi = chi H', d_R g_phph = 2R - chi^2 H') and the
+// redshift g = (-p.u_obs)/(-p.u_em) with -p.u_obs = E_loc = 1 (Eq. 73).
+// Returns false where no timelike prograde circular orbit exists.
+__device__ __forceinline__ bool emitter_g(const MetricConsts<double>& m, double R, double E,
+                                          double ell, double& g) {
+  double iR = 1.0 / R, H, dH;
+  lapse(m, R, iR, H, dH);
+  double den = 2.0 * R - m.chi2 * dH;
+  double disc = 2.0 * R * dH;
+  if (!(disc >= 0.0) || den == 0.0) return false;
+  double W = (-m.chi * dH + sqrt(disc)) / den;
+  double gtt = -H, gtp = -m.chi * (1.0 - H), gpp = R * R + m.chi2 + m.chi2 * (1.0 - H);
+  double norm = -(gtt + 2.0 * W * gtp + W * W * gpp);
+  if (!(norm > 0.0)) return false;
+  double uT = 1.0 / sqrt(norm);
+  g = 1.0 / (uT * (E - W * ell));
+  return true;
+}
+
+// Thin-disk emissivity, Eqs. (83)-(86) at z = 0, rho = R.
+__device__ __forceinline__ double emissivity_eq(const ImgParams& ip, double R) {
+  double tin = 0.5 * (1.0 + tanh((R - ip.R_in) / ip.sig_in));
+  double tout = 0.5 * (1.0 - tanh((R - ip.R_out) / ip.sig_out));
+  return ip.j0 * pow(R / ip.R_in, -ip.p) * exp(-(R - ip.R_in) / ip.R_s) * tin * tout;
+}
+
+// Event bookkeeping common to both precisions.
+struct CrossState {
+  double I[4];      // I_tot, I_0, I_1, I_2
+  double lam_last;  // affine parameter of the last trusted crossing
+  int32_t ncross;
+  bool have_trusted;
+};
+
+// Where a base ray's transfer maps go (image level 0 or points mode).
+struct CrossOut {
+  float* R_em;
+  float* phi_em;
+  float* T_em;
+  float* g;
+  int64_t stride, pix;   // plane stride (npix) and pixel index; pix < 0: none
+  bh_ray_record* rec;    // points mode
+};
+
+// Equatorial crossing inside one accepted step, evaluated in FP64 on the
+// step's dense output (Sec. 3.3 and Sec. 4.2): sign change of theta - pi/2
+// (an end point exactly on the plane belongs to the step that reaches it),
+// root by Illinois-modified regula falsi, trusted-crossing filter, then the
+// transfer maps (Eq. 82), redshift (Eq. 89) and g^3 j (Eqs. 83, 88).
+static __device__ __noinline__ void handle_crossing(const ImgParams& ip, const MetricConsts<double>& m,
+                                             double E, double ell, const double* y0,
+                                             const double* y1, const double* hf0,
+                                             const double* hf1, const double* hd, double lam,
+                                             double h, CrossState& cs, const CrossOut& co) {
+  const double s0 = y0[2] - kHalfPi, s1 = y1[2] - kHalfPi;
+  if (!((s0 > 0.0 && s1 <= 0.0) || (s0 < 0.0 && s1 >= 0.0))) return;
+  double sig = 1.0;
+  if (s1 != 0.0) {
+    double x0 = 0.0, f0 = s0, x1 = 1.0, f1 = s1;
+    for (int it = 0; it < 80; ++it) {
+      double x2 = x1 - f1 * (x1 - x0) / (f1 - f0);
+      if (!(x2 > fmin(x0, x1) && x2 < fmax(x0, x1))) x2 = 0.5 * (x0 + x1);
+      double f2 = dense1(y0[2], y1[2], hf0[2], hf1[2], hd[2], x2) - kHalfPi;
+      if (f2 == 0.0) {
+        x1 = x2;
+        break;
+      }
+      if ((f2 > 0.0) != (f1 > 0.0)) {
+        x0 = x1;
+        f0 = f1;
+      } else {
+        f0 *= 0.5;
+      }
+      x1 = x2;
+      f1 = f2;
+      if (fabs(x1 - x0) <= 1e-15 || fabs(f2) <= 1e-15) break;
+    }
+    sig = x1;
+  }
+  double yc[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) yc[i] = dense1(y0[i], y1[i], hf0[i], hf1[i], hd[i], sig);
+  double cth = cos(yc[2]);
+  double Sig = yc[1] * yc[1] + m.chi2 * cth * cth;
+  double thdot = yc[5] / Sig;                                   // Eq. (60)
+  double lamc = lam + sig * h;
+  bool trusted = fabs(thdot) >= ip.thdot_min &&
+                 (!cs.have_trusted || lamc - cs.lam_last >= ip.dlam_min);
+  if (!trusted) return;
+  int n = cs.ncross;
+  double g = 0.0, j = 0.0;
+  if (emitter_g(m, yc[1], E, ell, g)) j = emissivity_eq(ip, yc[1]);
+  double In = g * g * g * j;
+  cs.I[0] += In;
+  if (n < 3) {
+    cs.I[1 + n] = In;
+    double ph = fmod(yc[3], kTwoPi);
+    if (ph < 0.0) ph += kTwoPi;
+    if (co.pix >= 0) {
+      int64_t o = n * co.stride + co.pix;
+      if (co.R_em) co.R_em[o] = (float)yc[1];
+      if (co.phi_em) co.phi_em[o] = (float)ph;
+      if (co.T_em) co.T_em[o] = (float)yc[0];
+      if (co.g) co.g[o] = (float)g;
+    }
+    if (co.rec) {
+      co.rec->R_em[n] = yc[1];
+      co.rec->phi_em[n] = ph;
+      co.rec->T_em[n] = yc[0];
+      co.rec->g[n] = g;
+    }
+  }
+  cs.ncross = n + 1;
+  cs.lam_last = lamc;
+  cs.have_trusted = true;
+}
+
+// FP64 ray state.
+struct Ray64 {
+  double y[6];     // T, R, th, phi, p_R, p_th
+  double f[6];     // f(y) (FSAL)
+  double h, lam;
+  double E, ell;
+  CrossState cs;
+  float hdrift;
+  int32_t nacc, nrej, steps;
+  bool rejected;
+};
+
+// Launch (Sec. 3.2): p^mu = u_o + n^(a) e_(a) with E_loc = 1 (Eq. 73),
+// lowered with g_{mu nu} (Eq. 74).  With g_Tphi + omega g_phph = 0 this gives
+// p_R = sqrt(g_RR) n^(R), p_th = sqrt(g_thth) n^(th), ell = sqrt(g_phph) n^(phi),
+// E = N_o + omega ell.  Then the Hairer-Wanner starting step (Solving ODEs I,
+// Sec. II.4) for an error estimator of order 4.  All in FP64.
+__device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricConsts<double>& m,
+                                           double X, double Y, Ray64& r) {
+  double d = sqrt(ip.r_obs * ip.r_obs + X * X + Y * Y);
+  double id = 1.0 / d;
+  r.y[0] = 0.0;
+  r.y[1] = ip.r_obs;
+  r.y[2] = ip.incl;
+  r.y[3] = 0.0;
+  r.y[4] = ip.sq_grr * (-ip.r_obs * id);
+  r.y[5] = ip.sq_gth * (-Y * id);
+  r.ell = ip.sq_gph * (-X * id);
+  r.E = ip.zamo_N + ip.zamo_w * r.ell;
+  double W, P2;
+  geo_rhs(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f, W, P2);
+  double d0 = 0, d1 = 0, sc[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    sc[i] = ip.atol + ip.rtol * fabs(r.y[i]);
+    d0 += (r.y[i] / sc[i]) * (r.y[i] / sc[i]);
+    d1 += (r.f[i] / sc[i]) * (r.f[i] / sc[i]);
+  }
+  d0 = sqrt(d0 / 6.0);
+  d1 = sqrt(d1 / 6.0);
+  double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+  double f1[6];
+  geo_rhs(m, r.E, r.ell, r.y[1] + h0 * r.f[1], r.y[2] + h0 * r.f[2], r.y[4] + h0 * r.f[4],
+          r.y[5] + h0 * r.f[5], f1, W, P2);
+  double d2 = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double q = (f1[i] - r.f[i]) / sc[i];
+    d2 += q * q;
+  }
+  d2 = sqrt(d2 / 6.0) / h0;
+  double mx = fmax(d1, d2);
+  double h1 = (mx <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / mx, 0.2);
+  r.h = fmin(100.0 * h0, h1);
+  r.lam = 0.0;
+  r.cs.lam_last = 0.0;
+  r.cs.have_trusted = false;
+  r.cs.ncross = 0;
+  r.cs.I[0] = r.cs.I[1] = r.cs.I[2] = r.cs.I[3] = 0.0;
+  r.rejected = false;
+  r.nacc = r.nrej = r.steps = 0;
+  r.hdrift = 0.f;
+}
+
+// Polar axis: a state that passed through theta = 0 or pi is mapped back
+// into (0, pi) by (theta, p_th, phi) -> (-theta or 2 pi - theta, -p_th,
+// phi + pi).  Returns true if it reflected.
+__device__ __forceinline__ bool reflect_axis(double& th, double& pth, double& ph) {
+  if (th >= 0.0 && th <= kPi) return false;
+  th = th < 0.0 ? -th : kTwoPi - th;
+  pth = -pth;
+  ph += kPi;
+  return true;
+}
+
+// One attempted FP64 step.  Returns 0 while the ray continues, else the
+// terminal status + 1 (1 escaped, 2 captured, 3 undetermined).
+__device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConsts<double>& m,
+                                          Ray64& r, const CrossOut& co) {
+  const double h = r.h;
+  double k[7][6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) k[0][i] = r.f[i];
+  bool bad = false;
+  double W = 0, P2oD = 1;
+#pragma unroll
+  for (int s = 1; s < 7; ++s) {
+    double ys[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < s; ++j) acc += kDP.a[s][j] * k[j][i];
+      ys[i] = r.y[i] + h * acc;
+    }
+    bool ok = geo_rhs(m, r.E, r.ell, ys[1], ys[2], ys[4], ys[5], k[s], W, P2oD);
+    bad |= !ok;
+  }
+  double y1[6], err2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double a5 = 0.0, ae = 0.0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      a5 += kDP.b[j] * k[j][i];
+      ae += kDP.e[j] * k[j][i];
+    }
+    y1[i] = r.y[i] + h * a5;
+    double sc = ip.atol + ip.rtol * fmax(fabs(r.y[i]), fabs(y1[i]));
+    double q = h * ae / sc;
+    err2 += q * q;
+  }
+  float err = (float)sqrt(err2 / 6.0);
+  r.steps++;
+  if (bad || !(err <= 1.f)) {
+    r.h = bad ? 0.5 * h : h * (double)step_factor(err, true);
+    r.rejected = true;
+    r.nrej++;
+    return r.steps >= ip.max_steps ? 3 : 0;
+  }
+  r.nacc++;
+  {
+    const double s0 = r.y[2] - kHalfPi, s1 = y1[2] - kHalfPi;
+    if ((s0 > 0.0 && s1 <= 0.0) || (s0 < 0.0 && s1 >= 0.0)) {
+      double hf0[6], hf1[6], hd[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        double a = 0.0;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) a += kDP.d[j] * k[j][i];
+        hd[i] = h * a;
+        hf0[i] = h * k[0][i];
+        hf1[i] = h * k[6][i];
+      }
+      handle_crossing(ip, m, r.E, r.ell, r.y, y1, hf0, hf1, hd, r.lam, h, r.cs, co);
+    }
+  }
+  r.lam += h;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    r.y[i] = y1[i];
+    r.f[i] = k[6][i];
+  }
+  if (reflect_axis(r.y[2], r.y[5], r.y[3])) {
+    double Wr, Pr;
+    geo_rhs(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f, Wr, Pr);
+  }
+  // null-constraint monitor at the new point (stage 7 = new point, FSAL)
+  float hdv = (float)(fabs(W) / P2oD);
+  if (hdv > r.hdrift) r.hdrift = hdv;
+  if (r.y[1] < ip.R_cap) return 2;
+  if (r.y[1] > ip.R_esc) return 1;
+  r.h = h * (double)step_factor(err, r.rejected);
+  r.rejected = false;
+  return r.steps >= ip.max_steps ? 3 : 0;
+}
+
+// A ray handed from one precision pass to the next.
+struct alignas(16) SpillRec {
+  double y[6];
+  double h, lam, E, ell;
+  double I[4];
+  double lam_last;
+  int64_t item;
+  uint32_t img;
+  float hdrift;
+  int32_t ncross, nacc, nrej, steps;
+  int32_t flags;  // bit 0 have_trusted, bit 1 rejected
+  int32_t pad;
+};
+
+__device__ __forceinline__ void spill_from64(const Ray64& r, int64_t item, uint32_t img,
+                                             SpillRec& s) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) s.y[i] = r.y[i];
+  s.h = r.h;
+  s.lam = r.lam;
+  s.E = r.E;
+  s.ell = r.ell;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s.I[i] = r.cs.I[i];
+  s.lam_last = r.cs.lam_last;
+  s.item = item;
+  s.img = img;
+  s.hdrift = r.hdrift;
+  s.ncross = r.cs.ncross;
+  s.nacc = r.nacc;
+  s.nrej = r.nrej;
+  s.steps = r.steps;
+  s.flags = (r.cs.have_trusted ? 1 : 0) | (r.rejected ? 2 : 0);
+  s.pad = 0;
+}
+
+__device__ __forceinline__ void resume64(const SpillRec& s, const MetricConsts<double>& m,
+                                         Ray64& r) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.y[i] = s.y[i];
+  r.h = s.h;
+  r.lam = s.lam;
+  r.E = s.E;
+  r.ell = s.ell;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.cs.I[i] = s.I[i];
+  r.cs.lam_last = s.lam_last;
+  r.cs.ncross = s.ncross;
+  r.cs.have_trusted = (s.flags & 1) != 0;
+  r.rejected = (s.flags & 2) != 0;
+  r.hdrift = s.hdrift;
+  r.nacc = s.nacc;
+  r.nrej = s.nrej;
+  r.steps = s.steps;
+  double W, P2;
+  geo_rhs(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f, W, P2);
+}
+
+// Resolves a fresh work item to its image, output pixel and screen point.
+__device__ __forceinline__ void resolve_item(const TraceArgs& a, int64_t idx, uint32_t& img,
+                                             int64_t& pix, double& X, double& Y) {
+  if (a.mode == 1) {
+    img = 0;
+    pix = -1;
+    X = a.xy[2 * idx];
+    Y = a.xy[2 * idx + 1];
+    return;
+  }
+  uint64_t key;
+  if (a.level == 0) {
+    img = (uint32_t)(idx / a.npix);
+    pix = idx - (int64_t)img * a.npix;
+    key = (uint64_t)pix << 16;
+  } else {
+    key = a.lv.key[idx];
+    img = a.lv.img[idx];
+    pix = -1;
+  }
+  cell_centre(a.ip[img], key, X, Y);
+}
+
+__device__ __forceinline__ CrossOut cross_out(const TraceArgs& a, int64_t item, uint32_t img) {
+  CrossOut co;
+  co.R_em = co.phi_em = co.T_em = co.g = nullptr;
+  co.stride = a.npix;
+  co.pix = -1;
+  co.rec = nullptr;
+  if (a.mode == 1) {
+    co.rec = &a.rec[item];
+  } else if (a.level == 0) {
+    const OutPtrs& o = a.out[img];
+    co.R_em = o.R_em;
+    co.phi_em = o.phi_em;
+    co.T_em = o.T_em;
+    co.g = o.g;
+    co.pix = item - (int64_t)img * a.npix;
+  }
+  return co;
+}
+
+// Terminal write of a ray: the per-ray record of its level (for refinement
+// and assembly), the base-ray planes, or the points-mode record.
+__device__ __forceinline__ void finish_ray(const TraceArgs& a, int64_t item, uint32_t img,
+                                           int status, const CrossState& cs, float hdrift,
+                                           int nacc, int nrej, double E, double ell,
+                                           double lam) {
+  if (a.mode == 1) {
+    bh_ray_record* rc = &a.rec[item];
+    rc->status = status;
+    rc->ncross = cs.ncross;
+    rc->n_accept = nacc;
+    rc->n_reject = nrej;
+    rc->I_tot = cs.I[0];
+    rc->I_n[0] = cs.I[1];
+    rc->I_n[1] = cs.I[2];
+    rc->I_n[2] = cs.I[3];
+    rc->E = E;
+    rc->ell = ell;
+    rc->h_drift = hdrift;
+    rc->lambda_end = lam;
+    return;
+  }
+  int nc = cs.ncross > 255 ? 255 : cs.ncross;
+  uint16_t cls = (uint16_t)(status | (nc << 8));
+  if (a.level == 0) {
+    int64_t n = (int64_t)a.n_items;
+    a.base_I[item] = cs.I[0];
+    a.base_I[n + item] = cs.I[1];
+    a.base_I[2 * n + item] = cs.I[2];
+    a.base_I[3 * n + item] = cs.I[3];
+    a.base_cls[item] = cls;
+    a.base_depth[item] = 0;
+    const OutPtrs& o = a.out[img];
+    int64_t pix = item - (int64_t)img * a.npix;
+    o.status[pix] = (uint8_t)status;
+    o.ncross[pix] = (uint8_t)nc;
+    if (o.h_drift) o.h_drift[pix] = hdrift;
+  } else {
+    int64_t c = a.lv.cap;
+    a.lv.I[item] = cs.I[0];
+    a.lv.I[c + item] = cs.I[1];
+    a.lv.I[2 * c + item] = cs.I[2];
+    a.lv.I[3 * c + item] = cs.I[3];
+    a.lv.cls[item] = cls;
+    a.lv.depth[item] = (uint8_t)a.level;
+  }
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Number of work items of this pass.
+__device__ __forceinline__ int64_t pass_items(const TraceArgs& a) {
+  if (a.source == 1) {
+    unsigned long long c = *a.spill_in_count;
+    return (int64_t)(c < (unsigned long long)a.spill_cap ? c : (unsigned long long)a.spill_cap);
+  }
+  if (a.mode == 0 && a.level > 0) {
+    unsigned long long c = a.hdr->count[a.level];
+    return (int64_t)(c < (unsigned long long)a.lv.cap ? c : (unsigned long long)a.lv.cap);
+  }
+  return a.n_items;
+}
+
+// Warp-aggregated claim of `need` lanes' next items from a queue cursor.
+__device__ __forceinline__ int64_t claim(unsigned long long* head, bool need, int lane) {
+  unsigned mask = __ballot_sync(kFull, need);
+  if (!mask) return -1;
+  int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(head, (unsigned long long)__popc(mask));
+  base = __shfl_sync(kFull, base, leader);
+  return need ? (int64_t)base + __popc(mask & ((1u << lane) - 1u)) : -1;
+}
+
+// Warp sum of lane tallies, one atomic per warp.
+__device__ __forceinline__ void flush_tally(unsigned long long* dst, unsigned long long v,
+                                            int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  if (lane == 0 && v) atomicAdd(dst, v);
+}
+
+}  // namespace bhrt

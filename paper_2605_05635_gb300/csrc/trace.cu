@@ -1,0 +1,113 @@
+// trace.cu -- persistent FP64 per-ray integrator kernel.
+//
+// One thread integrates one backward ray (Sec. 3-4): launch from the ZAMO
+// screen (Eqs. 63-74), Dormand-Prince 5(4) steps of Hamilton's equations
+// (Eqs. 57-62, separated form in bh_common.cuh), capture / escape
+// (Eq. 75, Sec. 3.3), equatorial-crossing events on the dense output
+// (Sec. 3.3, 4.2), transfer maps (Eq. 82), redshift (Eqs. 89-91) and the
+// thin-disk intensity g^3 j (Eqs. 83-88).
+//
+// Scheduling: a persistent grid; every warp keeps 32 rays in flight and
+// refills lanes whose ray has terminated with the next items of a global
+// queue (one warp-aggregated atomic per refill), so long near-critical rays
+// do not hold idle lanes hostage.
+//
+// In the all-FP64 path this kernel traces every ray.  In the mixed path it
+// is the promoted pass: it resumes rays handed over by the FP32 kernel and,
+// once a ray is outgoing beyond demote_R, hands it back for an FP32 finish.
+#include <cuda_runtime.h>
+
+#include "integrator.cuh"
+
+namespace bhrt {
+
+__global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_items = pass_items(a);
+  const unsigned long long budget = a.hdr->budget_ns;
+  const unsigned long long t0 = a.hdr->t_start;
+
+  Ray64 r;
+  MetricConsts<double> m;
+  const ImgParams* ip = a.ip;
+  int64_t item = -1;
+  uint32_t img = 0;
+  bool active = false, drained = false;
+  unsigned iter = 0;
+  unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_full = 0;
+
+  while (true) {
+    const bool need = !active && !drained;
+    int64_t idx = claim(a.head, need, lane);
+    if (need) {
+      if (idx < n_items) {
+        if (a.source == 1) {
+          const SpillRec& s = a.spill_in[idx];
+          item = s.item;
+          img = s.img;
+          ip = &a.ip[img];
+          m = metric_consts<double>(*ip);
+          resume64(s, m, r);
+        } else {
+          double X, Y;
+          int64_t pix;
+          item = idx;
+          resolve_item(a, idx, img, pix, X, Y);
+          ip = &a.ip[img];
+          m = metric_consts<double>(*ip);
+          ray_init64(*ip, m, X, Y, r);
+        }
+        active = true;
+      } else {
+        drained = true;
+      }
+    }
+    if (__ballot_sync(kFull, active) == 0) {
+      if (__ballot_sync(kFull, !drained) == 0) break;
+      continue;
+    }
+    if (active) {
+      const CrossOut co = cross_out(a, item, img);
+      const int acc0 = r.nacc, rej0 = r.nrej;
+      int term = ray_step64(*ip, m, r, co);
+      w_acc += (unsigned long long)(r.nacc - acc0);
+      w_rej += (unsigned long long)(r.nrej - rej0);
+      if (term) {
+        finish_ray(a, item, img, term - 1, r.cs, r.hdrift, r.nacc, r.nrej, r.E, r.ell, r.lam);
+        w_rays += 1ull;
+        active = false;
+      } else if (a.allow_spill && r.nacc != acc0 && r.y[1] > ip->demote_R && r.y[4] > 0.0) {
+        // outgoing beyond the strong-field zone: finish in FP32
+        unsigned long long slot = atomicAdd(a.spill_out_count, 1ull);
+        if (slot < (unsigned long long)a.spill_cap) {
+          spill_from64(r, item, img, a.spill_out[slot]);
+          active = false;
+        } else {
+          w_full += 1ull;
+        }
+      }
+    }
+    if (budget && ((++iter & 255u) == 0u)) {
+      unsigned long long now = __shfl_sync(kFull, globaltimer(), 0);
+      if (now - t0 > budget) {
+        if (lane == 0) atomicCAS(&a.hdr->status, 0, (int)BH_ERR_TIMEOUT);
+        break;
+      }
+    }
+  }
+  flush_tally(&a.hdr->accepted, w_acc, lane);
+  flush_tally(&a.hdr->rejected, w_rej, lane);
+  flush_tally(&a.hdr->rays[a.level], w_rays, lane);
+  flush_tally(&a.hdr->spill_full, w_full, lane);
+}
+
+cudaError_t launch_trace_fp64(const TraceArgs& a, LaunchShape s, cudaStream_t st) {
+  trace_fp64_kernel<<<s.blocks, s.threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t spill_record_bytes() { return sizeof(SpillRec); }
+
+const void* trace_fp64_kernel_ptr() { return (const void*)trace_fp64_kernel; }
+
+}  // namespace bhrt

@@ -1,0 +1,40 @@
+"""Runs one fixed tracing case a few times, for profiling a kernel in
+isolation (``ncu ... python -m paper_2605_05635_gb300.profile_case``).
+
+Cases: ``kerr128`` (Kerr a = 0.5, i = 17 deg, 128^2 over [-10, 10]^2, no
+refinement) and ``sweep512`` (one 512^2 image of the six-image sweep, with
+refinement).
+"""
+import argparse
+import math
+import sys
+
+import torch
+
+from . import bhrt, workloads
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="kerr128", choices=["kerr128", "sweep512"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--repeat", type=int, default=2)
+    a = ap.parse_args(argv)
+    if a.case == "kerr128":
+        flat = dict(workloads.kerr_64(), nx=128, ny=128)
+    else:
+        flat = workloads.sweep_512()[0]
+    flat["precision"] = bhrt.FP64 if a.precision == "fp64" else bhrt.MIXED
+    items = [bhrt.from_flat(flat)]
+    plan = bhrt.Plan(items)
+    for _ in range(a.repeat):
+        plan.launch()
+    torch.cuda.synchronize()
+    plan.check()
+    st = plan.stats()
+    print(f"case {a.case} {a.precision}: rays {sum(st['rays'])} accepted {st['accepted_steps']}")
+    plan.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,121 @@
+"""GPU parity of the mixed-precision path (FP32 bulk, FP64 promoted) against
+the FP64 oracle.
+
+Bar: intensity within 1e-4 of the image maximum; integer planes exact except
+on rays whose class is not determined at the mixed path's precision (the
+oracle's own class changes under a relative screen perturbation of 1e-6 or
+when its tolerance moves between the mixed path's 1e-8 and 1e-12).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from parity import oracle_flat, pixel_centre
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_05635_gb300 as B
+    B.lib()
+    return B
+
+
+def class_sensitive(oracle, flat, X, Y, eps=1e-6):
+    base = oracle_flat(flat, oracle)
+    pts = [[X, Y]]
+    d = eps * max(abs(X), abs(Y), 1.0)
+    pts += [[X + d, Y], [X - d, Y], [X, Y + d], [X, Y - d]]
+    classes = set()
+    for rtol in (1e-8, 1e-12):
+        P = oracle.problem(**{**base, "rtol": rtol, "atol": rtol * 1e-2})
+        for r in oracle.trace_points(P, pts):
+            classes.add((int(r["status"]), int(r["ncross"])))
+    return len(classes) > 1
+
+
+def _mixed_flat(workloads, **kw):
+    return dict(workloads.kerr_64(), **workloads.MIXED_INTEG, **kw)
+
+
+def test_mixed_kerr_64(B, oracle):
+    from paper_2605_05635_gb300 import workloads
+    flat = _mixed_flat(workloads)
+    st, cam, em, it = B.from_flat(flat)
+    out = {k: v.cpu().numpy() for k, v in B.trace_image(st, cam, em, it).items()}
+    ref = oracle.trace_image(oracle.problem(**{**oracle_flat(flat, oracle), "rtol": 1e-10,
+                                               "atol": 1e-12}))
+    bad = np.argwhere((out["status"] != ref["status"]) | (out["ncross"] != ref["ncross"]))
+    for j, i in bad:
+        assert class_sensitive(oracle, flat, *pixel_centre(flat, i, j)), (i, j)
+    assert len(bad) <= 0.005 * out["status"].size + 1
+    ok = np.ones(out["status"].shape, bool)
+    for j, i in bad:
+        ok[j, i] = False
+    scale = np.abs(ref["I"]).max()
+    err = np.max(np.abs(out["I"][ok] - ref["I"][ok])) / scale
+    assert err <= TOL_MIXED, err
+    for n in range(3):
+        assert np.max(np.abs(out["I_n"][n][ok] - ref["I_n"][n][ok])) <= TOL_MIXED * scale
+        has = ok & (ref["ncross"] > n) & (ref["g"][n] != 0)
+        if has.any():
+            r = ref["R_em"][n][has]
+            assert np.max(np.abs(out["R_em"][n][has] - r) / r) <= 1e-5
+
+
+@pytest.mark.parametrize("metric,incl", [(0, 80.0), (1, 17.0), (2, 50.0)])
+def test_mixed_refined_vs_fp64(B, oracle, metric, incl):
+    """Mixed vs the GPU FP64 path (itself pinned to the oracle) and vs the
+    oracle on a refined ragged screen: intensity within 1e-4 of the maximum
+    away from pixels whose class is undetermined at mixed precision."""
+    from paper_2605_05635_gb300 import workloads
+    flat = _mixed_flat(workloads, metric=metric, chi=0.9, incl=math.radians(incl), nx=22,
+                       ny=18, x_min=-12.0, x_max=12.0, y_min=-10.0, y_max=10.0, levels=2,
+                       **workloads.HALO[metric])
+    st, cam, em, it = B.from_flat(flat)
+    mx = {k: v.cpu().numpy() for k, v in B.trace_image(st, cam, em, it, keys_cap=1 << 20).items()}
+    ref = oracle.trace_image(oracle.problem(**{**oracle_flat(flat, oracle), "rtol": 1e-10,
+                                               "atol": 1e-12}))
+    scale = np.abs(ref["I"]).max()
+    bad = np.argwhere((mx["status"] != ref["status"]) | (mx["ncross"] != ref["ncross"]))
+    for j, i in bad:
+        assert class_sensitive(oracle, flat, *pixel_centre(flat, i, j)), (i, j)
+    diff = np.abs(mx["I"] - ref["I"]) / scale
+    worst = np.argwhere(diff > TOL_MIXED)
+    # a pixel beyond the bar must owe it to a refinement cell whose class is
+    # undetermined at mixed precision: its subtree differs from the oracle's
+    gk = np.sort(mx["refine_keys"].astype(np.uint64))
+    base_of = lambda k: (k >> np.uint64(16)).astype(np.int64)
+    for j, i in worst:
+        q = j * flat["nx"] + i
+        mine = np.sort(gk[base_of(gk) == q])
+        theirs = ref["keys"][base_of(ref["keys"]) == q]
+        assert not np.array_equal(mine, theirs) or (j, i) in [tuple(b) for b in bad], \
+            f"pixel ({i},{j}) err {diff[j, i]:.2e} with identical refinement"
+    assert len(worst) <= 0.02 * diff.size + 1
+
+
+def test_mixed_points_match_oracle(B, oracle):
+    from paper_2605_05635_gb300 import workloads
+    flat = _mixed_flat(workloads, metric=2, chi=0.94, incl=math.radians(17.0),
+                       **workloads.HALO[2])
+    rng = np.random.default_rng(3)
+    xy = rng.uniform(-11, 11, (96, 2))
+    st, cam, em, it = B.from_flat(flat)
+    g = B.trace_points(st, cam, em, it, xy)
+    r = oracle.trace_points(oracle.problem(**{**oracle_flat(flat, oracle), "rtol": 1e-10,
+                                              "atol": 1e-12}), xy)
+    scale = max(float(np.max(r["I_tot"])), 1e-30)
+    for k in range(len(xy)):
+        if (g[k]["status"], g[k]["ncross"]) != (r[k]["status"], r[k]["ncross"]):
+            assert class_sensitive(oracle, flat, *xy[k])
+            continue
+        assert abs(g[k]["I_tot"] - r[k]["I_tot"]) <= TOL_MIXED * scale
+        assert g[k]["E"] == pytest.approx(r[k]["E"], rel=1e-14)

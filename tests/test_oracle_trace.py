@@ -207,3 +207,18 @@ def test_lensing_band_structure(oracle):
     assert (img["ncross"] == 1).sum() > 100
     assert (img["ncross"] >= 2).sum() > 0
     assert img["ncross"][0, 0] in (0, 1)
+
+
+def test_polar_axis_ray_matches_rotated_ray_in_schwarzschild(oracle):
+    """A ray launched at X = 0 has ell ~ 0 and passes through the polar axis
+    (reflected back into (0, pi)).  In Schwarzschild the orbit depends only on
+    the impact parameter: its fate follows K/E^2 < 27 like the same impact
+    parameter at another position angle (which never nears the axis), and the
+    separation constant is conserved across the axis passage."""
+    P = oracle.problem(metric=oracle.KERR, chi=0.0, incl=math.radians(30.0))
+    for b in (4.0, 5.1, 5.3, 5.5, 7.0):
+        pol, rot = oracle.trace_points(P, [[0.0, b], [b, 0.0]])
+        k = pol["K0"] / pol["E"] ** 2
+        assert pol["status"] == rot["status"] == (1 if k < 27.0 else 0)
+        assert abs(pol["K_final"] - pol["K0"]) <= 1e-9 * pol["K0"]
+        assert pol["n_accept"] < 2 * rot["n_accept"]
