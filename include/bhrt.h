@@ -227,6 +227,47 @@ bh_status bh_plan_set_timing(bh_plan plan, int32_t enable);
 bh_status bh_plan_stats(bh_plan plan, void* stream, bh_run_stats* out);
 bh_status bh_plan_destroy(bh_plan plan);
 
+/* ---------------------------------------------------------------------- */
+/* Image diagnostics of Sec. 6.2-6.3 from a traced intensity plane I
+ * (device float [ny][nx], screen geometry from cam).  out12 (device,
+ * 12 doubles) receives, in order:
+ *   F (Eq. 92), X_c, Y_c (Eq. 93), C (Eq. 94), rho_bar (Eq. 96),
+ *   d_img (Eq. 97), w_img (Eq. 98), A_LR (Eqs. 99-100), P = I_max / mean of
+ *   I over pixels with I > 0 (Eq. 101), rho_peak, d_peak = 2 rho_peak
+ *   (Eq. 106), theta_peak = d_peak theta_g (Eq. 107).
+ * Integrals are pixel sums times dX dY at pixel centres; the left/right split
+ * uses strict inequalities; the radial profile bins rho_0 (Eq. 105) with
+ * width dX from 0, takes the mean per non-empty bin, resolves argmax ties to
+ * the smaller radius and reports the bin centre.  All accumulation is FP64.
+ * Needs bh_diagnostics_workspace_size bytes of 256-byte aligned workspace. */
+bh_status bh_diagnostics_workspace_size(const bh_camera* cam, size_t* bytes);
+bh_status bh_diagnostics(const float* I, const bh_camera* cam, double theta_g, double* out12,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* Visibilities of Eq. (108), FP64 direct sum: V_k = sum_ij I_ij
+ * exp[-2 pi i (u_k X_i + v_k Y_j)] dX dY for K baselines uv[2k], uv[2k+1]
+ * in cycles per M (device doubles); V[2k], V[2k+1] = Re, Im (device).
+ * The normalised amplitude of Eq. (109) is |V_k| / |V(0,0)| with
+ * V(0,0) = F.  Cost O(K nx ny) in FP64: the reference mode. */
+bh_status bh_visibilities_fp64(const float* I, const bh_camera* cam, const double* uv, int64_t K,
+                               double* V, void* stream);
+
+/* Visibilities of Eq. (108) as a tensor-core contraction (tcgen05):
+ *   mode 0: FP64 direct sum (bh_visibilities_fp64; workspace unused);
+ *   mode 1: operands split hi + lo in BF16, FP32 accumulation;
+ *   mode 2: operands split hi + lo in FP16, FP32 accumulation (the image is
+ *           divided by image_max first, so intensities far below the maximum
+ *           lose relative precision to the FP16 exponent range).
+ * image_max > 0 is the image maximum (or any positive scale near it), used
+ * to normalise before splitting.  uv and V as in bh_visibilities_fp64.
+ * Modes 1-2 need nx <= 4096 and bh_visibilities_workspace_size bytes of
+ * 256-byte aligned workspace; a stalled pipeline wait (bounded) sets
+ * BH_ERR_TIMEOUT in the workspace status word (bh_workspace_status). */
+bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes);
+bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
+                          int32_t mode, double image_max, double* V, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
 /* Device status word of the last call that used this workspace (blocking
  * copy; call after synchronising the stream). */
 bh_status bh_workspace_status(const void* workspace, void* stream);

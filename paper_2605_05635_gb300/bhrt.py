@@ -218,6 +218,17 @@ def lib():
         L.bh_plan_set_timing.argtypes = [C.c_void_p, C.c_int32]
         L.bh_plan_stats.argtypes = [C.c_void_p, C.c_void_p, P(RunStats)]
         L.bh_plan_destroy.argtypes = [C.c_void_p]
+        L.bh_diagnostics_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
+        L.bh_diagnostics.argtypes = [C.c_void_p, P(_Camera), C.c_double, C.c_void_p, C.c_void_p,
+                                     C.c_size_t, C.c_void_p]
+        L.bh_visibilities_fp64.argtypes = [C.c_void_p, P(_Camera), C.c_void_p, C.c_int64,
+                                           C.c_void_p, C.c_void_p]
+        L.bh_visibilities_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
+        L.bh_visibilities.argtypes = [C.c_void_p, P(_Camera), C.c_void_p, C.c_int64, C.c_int32,
+                                      C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        for fn in ("bh_diagnostics_workspace_size", "bh_diagnostics", "bh_visibilities_fp64",
+                   "bh_visibilities_workspace_size", "bh_visibilities"):
+            getattr(L, fn).restype = C.c_int
         for fn in ("bh_host_geometry", "bh_workspace_size", "bh_trace_image", "bh_trace_batch",
                    "bh_points_workspace_size", "bh_trace_points", "bh_workspace_status",
                    "bh_plan_create", "bh_plan_launch", "bh_plan_set_timing", "bh_plan_stats",
@@ -409,3 +420,68 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+DIAG_NAMES = ["F", "X_c", "Y_c", "C", "rho_bar", "d_img", "w_img", "A_LR", "P", "rho_peak",
+              "d_peak", "theta_peak"]
+
+
+def diagnostics(I: torch.Tensor, cam: Camera, theta_g: float = 1.0, stream=None,
+                out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None):
+    """Sec. 6.2-6.3 diagnostics of a device intensity plane; returns a device
+    tensor of 12 doubles (see DIAG_NAMES)."""
+    if I.dtype != torch.float32 or not I.is_cuda or not I.is_contiguous():
+        raise ValueError("I must be a contiguous float32 CUDA tensor")
+    nb = C.c_size_t(0)
+    _check(lib().bh_diagnostics_workspace_size(C.byref(cam._c()), C.byref(nb)),
+           "bh_diagnostics_workspace_size")
+    if workspace is None or workspace.numel() < nb.value:
+        workspace = _aligned_workspace(nb.value, I.device)
+    if out is None:
+        out = torch.empty(12, dtype=torch.float64, device=I.device)
+    _check(lib().bh_diagnostics(C.c_void_p(I.data_ptr()), C.byref(cam._c()), theta_g,
+                                C.c_void_p(out.data_ptr()), C.c_void_p(workspace.data_ptr()),
+                                workspace.numel(), _stream_ptr(stream)), "bh_diagnostics")
+    return out
+
+
+def visibilities_fp64(I: torch.Tensor, cam: Camera, uv: torch.Tensor, stream=None,
+                      out: Optional[torch.Tensor] = None):
+    """Eq. (108) by the FP64 direct sum; returns a complex128 device tensor."""
+    uv = uv.to(device=I.device, dtype=torch.float64).contiguous()
+    K = uv.shape[0]
+    if out is None:
+        out = torch.empty(K, 2, dtype=torch.float64, device=I.device)
+    _check(lib().bh_visibilities_fp64(C.c_void_p(I.data_ptr()), C.byref(cam._c()),
+                                      C.c_void_p(uv.data_ptr()), K, C.c_void_p(out.data_ptr()),
+                                      _stream_ptr(stream)), "bh_visibilities_fp64")
+    return torch.view_as_complex(out)
+
+
+VIS_FP64, VIS_BF16, VIS_FP16 = 0, 1, 2
+
+
+def visibilities(I: torch.Tensor, cam: Camera, uv: torch.Tensor, mode: int = VIS_BF16,
+                 image_max: Optional[float] = None, stream=None, out=None, workspace=None,
+                 check: bool = True):
+    """Eq. (108) on the tensor cores (split BF16 / FP16) or by the FP64 direct
+    sum (mode 0); returns a complex128 device tensor."""
+    uv = uv.to(device=I.device, dtype=torch.float64).contiguous()
+    K = uv.shape[0]
+    if image_max is None:
+        image_max = float(I.abs().max().item()) or 1.0
+    if out is None:
+        out = torch.empty(K, 2, dtype=torch.float64, device=I.device)
+    nb = C.c_size_t(0)
+    _check(lib().bh_visibilities_workspace_size(C.byref(cam._c()), C.byref(nb)),
+           "bh_visibilities_workspace_size")
+    if workspace is None or workspace.numel() < nb.value:
+        workspace = _aligned_workspace(nb.value, I.device)
+    sp = _stream_ptr(stream)
+    _check(lib().bh_visibilities(C.c_void_p(I.data_ptr()), C.byref(cam._c()),
+                                 C.c_void_p(uv.data_ptr()), K, mode, image_max,
+                                 C.c_void_p(out.data_ptr()), C.c_void_p(workspace.data_ptr()),
+                                 workspace.numel(), sp), "bh_visibilities")
+    if check and mode != VIS_FP64:
+        _check(lib().bh_workspace_status(C.c_void_p(workspace.data_ptr()), sp), "device status")
+    return torch.view_as_complex(out)

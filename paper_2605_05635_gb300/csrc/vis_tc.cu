@@ -1,0 +1,466 @@
+// vis_tc.cu -- visibilities (Sec. 6.4, Eq. 108) as a dense image-by-phase
+// contraction on the 5th-generation tensor cores (tcgen05, TMEM, TMA).
+//
+// exp[-2 pi i (u X_i + v Y_j)] = exp(-2 pi i u X_i) exp(-2 pi i v Y_j), so with
+//   C_kj = sum_i cos(2 pi u_k X_i) I_ji,   S_kj = sum_i sin(2 pi u_k X_i) I_ji
+// (a GEMM: rows = baselines x {cos, sin}, columns = image rows j, reduction
+// over image columns i), the visibility is
+//   Re V_k = sum_j [cos(2 pi v_k Y_j) C_kj - sin(2 pi v_k Y_j) S_kj] dX dY,
+//   Im V_k = -sum_j [sin(2 pi v_k Y_j) C_kj + cos(2 pi v_k Y_j) S_kj] dX dY.
+// Precision: both operands are split into hi + lo parts in BF16 (or FP16)
+// and the three significant products hi*hi + hi*lo + lo*hi are accumulated in
+// FP32 in tensor memory, by concatenating along the reduction axis:
+//   A' = [A_hi | A_hi | A_lo],  B' = [B_hi | B_lo | B_hi].
+//
+// One CTA owns 64 baselines (128 accumulator rows: 64 cos + 64 sin) and
+// sweeps the image rows in passes of 512 columns of tensor memory.  Phase
+// tiles of A' are generated on chip straight into shared memory in the
+// 128-byte-swizzled K-major layout; image tiles of B' arrive by TMA in the
+// same layout.  Two pipeline stages overlap phase generation and TMA with the
+// MMAs of the previous chunk.  The epilogue reads the accumulators with
+// tcgen05.ld, applies the v-phases and reduces over j.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace bhrt {
+
+constexpr int kVisRows = 128;       // accumulator lanes (64 baselines x cos/sin)
+constexpr int kVisUV = 64;          // baselines per CTA
+constexpr int kVisKC = 64;          // reduction chunk (elements): 128 bytes of 16-bit
+constexpr int kVisNP = 512;         // image rows per pass (TMEM columns)
+constexpr int kVisThreads = 256;
+constexpr int kStages = 2;
+constexpr int kAStage = kVisRows * kVisKC * 2;   // 16 KB
+constexpr int kBStage = kVisNP * kVisKC * 2;     // 64 KB
+constexpr int kVisMaxNx = 4096;    // bound of the per-CTA phase table
+constexpr int kVisSmem = kStages * (kAStage + kBStage) + 1024 + 256 + 2048 +
+                         kVisUV * (kVisMaxNx / kVisKC) * 4;
+constexpr unsigned kSpinLimit = 1u << 26;
+
+struct VisArgs {
+  const double* uv;   // [K][2]
+  int64_t K;
+  int nx, ny, nxp;    // nxp = nx rounded up to kVisKC
+  double x_min, y_min, dx, dy;
+  double scale;       // image scale applied before splitting (undone at the end)
+  int fp16;           // 0: BF16 operands, 1: FP16 operands
+  double* V;          // [K][2]
+  int* status;        // device status word (spin-limit exceeded)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait on an mbarrier phase; returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  uint32_t a = smem_u32(bar);
+  for (unsigned it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Shared-memory matrix descriptor for tcgen05.mma: K-major operand in the
+// 128-byte swizzled layout (8-row x 128-byte atoms, atoms 1024 bytes apart).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (16 B, unused)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: 1024 B
+  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100)
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A/B BF16 or FP16,
+// both K-major, M = 128, N = 256.
+__device__ __forceinline__ uint32_t instr_desc(bool fp16) {
+  uint32_t d = 0;
+  d |= 1u << 4;                         // D format: F32
+  d |= (fp16 ? 0u : 1u) << 7;           // A format: F16 = 0, BF16 = 1
+  d |= (fp16 ? 0u : 1u) << 10;          // B format
+  d |= (uint32_t)(256 >> 3) << 17;      // N / 8
+  d |= (uint32_t)(128 >> 4) << 24;      // M / 16
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <class T16>
+__device__ __forceinline__ uint16_t to_bits(T16 x) {
+  return *reinterpret_cast<uint16_t*>(&x);
+}
+
+__device__ __forceinline__ void split16(float v, bool fp16, uint16_t& hi, uint16_t& lo) {
+  if (fp16) {
+    __half h = __float2half_rn(v);
+    __half l = __float2half_rn(v - __half2float(h));
+    hi = to_bits(h);
+    lo = to_bits(l);
+  } else {
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    hi = to_bits(h);
+    lo = to_bits(l);
+  }
+}
+
+// Image -> B' = [hi | lo | hi] rows of length 3 * nxp (zero padded).
+__global__ void vis_prepare_image(const float* I, VisArgs a, uint16_t* Bp) {
+  const int64_t n = (int64_t)a.ny * a.nxp;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int j = (int)(q / a.nxp), i = (int)(q % a.nxp);
+    float v = i < a.nx ? (float)((double)I[(int64_t)j * a.nx + i] * a.scale) : 0.f;
+    uint16_t hi, lo;
+    split16(v, a.fp16 != 0, hi, lo);
+    uint16_t* row = Bp + (int64_t)j * 3 * a.nxp;
+    row[i] = hi;
+    row[a.nxp + i] = lo;
+    row[2 * a.nxp + i] = hi;
+  }
+}
+
+__global__ void __launch_bounds__(kVisThreads, 1)
+    vis_tc_kernel(const __grid_constant__ CUtensorMap bmap, VisArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sA = smem;                                // [stages][16 KB]
+  unsigned char* sB = smem + kStages * kAStage;            // [stages][64 KB]
+  uint64_t* bar_full = reinterpret_cast<uint64_t*>(sB + kStages * kBStage);  // TMA landed
+  uint64_t* bar_mma = bar_full + kStages;                  // MMAs of a stage done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_mma + kStages);
+  int* fail = reinterpret_cast<int*>(tmem_slot + 1);       // CTA-uniform failure flag
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);    // epilogue exchange [2][128][2]
+  float* tbase = red + 512;                                // [64][nxp / 64] phase table
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t uv0 = (int64_t)blockIdx.x * kVisUV;
+  const bool fp16 = a.fp16 != 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_mma[s], 1);
+    }
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  // per-thread baseline constants for phase generation: this thread fills
+  // rows r (cos) and r + 64 (sin) for baseline kk = tid % 64, columns
+  // tid / 64 + 4 q of each chunk.
+  const int kk = tid & 63;
+  const int col0 = tid >> 6;              // 0..3
+  const int64_t kidx = uv0 + kk;
+  const double u = kidx < a.K ? a.uv[2 * kidx] : 0.0;
+  const float two_u_dx = (float)(2.0 * u * a.dx);
+  // phase table: 2 u X_{64 b} reduced mod 2, once per CTA in FP64
+  const int nblk = a.nxp / kVisKC;
+  for (int b = col0; b < nblk; b += 4) {
+    double t = 2.0 * u * (a.x_min + (kVisKC * b + 0.5) * a.dx);
+    tbase[kk * nblk + b] = (float)(t - 2.0 * rint(0.5 * t));
+  }
+  __syncthreads();
+
+  const int chunks = 3 * a.nxp / kVisKC;
+  const int passes = (a.ny + kVisNP - 1) / kVisNP;
+  const uint32_t idesc = instr_desc(fp16);
+  bool ok = true;
+  unsigned use[kStages] = {0, 0};         // completed uses per stage (for parity)
+  // epilogue accumulators for the thread's (row, column-half): P = sum c D, Q = sum s D
+  float accP = 0.f, accQ = 0.f;
+  const int erow = (warp & 3) * 32 + lane;          // TMEM lane this thread reads
+  const int ehalf = warp >> 2;                      // which 256-column half
+  const int64_t ek = uv0 + (erow & 63);
+  const double ev = ek < a.K ? a.uv[2 * ek + 1] : 0.0;
+
+  for (int pass = 0; pass < passes && ok; ++pass) {
+    for (int c = 0; c < chunks && ok; ++c) {
+      const int s = (pass * chunks + c) % kStages;
+      // wait (one thread, bounded) for the MMAs that last used this stage
+      if (tid == 0 && use[s] > 0 && !mbar_wait(&bar_mma[s], (use[s] - 1) & 1)) *fail = 1;
+      __syncthreads();
+      if (*fail) {
+        ok = false;
+        break;
+      }
+      if (tid == 0) {
+        mbar_expect_tx(&bar_full[s], kBStage);
+        tma_load_2d(sB + s * kBStage, &bmap, c * kVisKC, pass * kVisNP, &bar_full[s]);
+        tma_load_2d(sB + s * kBStage + kBStage / 2, &bmap, c * kVisKC, pass * kVisNP + 256,
+                    &bar_full[s]);
+      }
+      // phase tile of A': third t of the reduction axis
+      const int kg = c * kVisKC;
+      const int third = kg / a.nxp;
+      const int i0 = kg - third * a.nxp;
+      const bool want_lo = third == 2;
+      // base argument 2 u X_{i0} (mod 2) from the table, increments in FP32
+      const float t0 = tbase[kk * nblk + i0 / kVisKC];
+      unsigned char* At = sA + s * kAStage;
+#pragma unroll 4
+      for (int q = 0; q < kVisKC / 4; ++q) {
+        const int col = col0 + 4 * q;
+        float arg = t0 + (float)col * two_u_dx;
+        float sn, cs;
+        sincospif(arg, &sn, &cs);
+        uint16_t ch, cl, sh, sl;
+        split16(cs, fp16, ch, cl);
+        split16(sn, fp16, sh, sl);
+        const uint16_t cv = want_lo ? cl : ch, sv = want_lo ? sl : sh;
+        // 128-byte swizzle: 16-byte chunk index (col / 8) xor (row % 8)
+        const int chunk16 = col >> 3, within = (col & 7) * 2;
+        const int r0 = kk, r1 = kk + 64;
+        *reinterpret_cast<uint16_t*>(At + r0 * 128 + ((chunk16 ^ (r0 & 7)) << 4) + within) = cv;
+        *reinterpret_cast<uint16_t*>(At + r1 * 128 + ((chunk16 ^ (r1 & 7)) << 4) + within) = sv;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        if (!mbar_wait(&bar_full[s], use[s] & 1)) {
+          *fail = 1;
+        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t aaddr = smem_u32(At), baddr = smem_u32(sB + s * kBStage);
+#pragma unroll
+          for (int kk16 = 0; kk16 < kVisKC / 16; ++kk16) {
+            const uint64_t ad = smem_desc_sw128(aaddr + kk16 * 32);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t bd = smem_desc_sw128(baddr + h * (kBStage / 2) + kk16 * 32);
+              mma_f16(tmem + h * 256, ad, bd, idesc, c > 0 || kk16 > 0);
+            }
+          }
+          mma_commit(&bar_mma[s]);
+        }
+      }
+      use[s]++;
+      __syncthreads();
+      if (*fail) ok = false;
+    }
+    if (!ok) break;
+    // all MMAs of this pass: wait for the last commit (MMAs complete in order)
+    const int last = (pass * chunks + chunks - 1) % kStages;
+    if (tid == 0 && !mbar_wait(&bar_mma[last], (use[last] - 1) & 1)) *fail = 1;
+    __syncthreads();
+    if (*fail) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const double tvp = 2.0 * ev * (a.y_min + (pass * kVisNP + ehalf * 256 + 0.5) * a.dy);
+    const float tv0 = (float)(tvp - 2.0 * rint(0.5 * tvp));
+    const float dv = (float)(2.0 * ev * a.dy);
+    // epilogue: this thread reads lane erow, columns ehalf*256 .. +256
+    for (int cb = 0; cb < 256; cb += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ehalf * 256 + cb);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+          "%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int jb = pass * kVisNP + ehalf * 256 + cb;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        if (jb + e >= a.ny) break;
+        float sn, cs;
+        sincospif(tv0 + (float)(cb + e) * dv, &sn, &cs);
+        const float D = __uint_as_float(r[e]);
+        accP = fmaf(cs, D, accP);
+        accQ = fmaf(sn, D, accQ);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  // combine: rows kk (C) and kk + 64 (S), two column halves each
+  red[ehalf * 256 + erow * 2 + 0] = accP;
+  red[ehalf * 256 + erow * 2 + 1] = accQ;
+  __syncthreads();
+  if (tid < kVisUV && ok) {
+    const int64_t k = uv0 + tid;
+    if (k < a.K) {
+      float P1 = 0, P2 = 0, Q1 = 0, Q2 = 0;  // sum cC, sum sC, sum sS, sum cS
+      for (int hh = 0; hh < 2; ++hh) {
+        P1 += red[hh * 256 + tid * 2 + 0];
+        P2 += red[hh * 256 + tid * 2 + 1];
+        Q2 += red[hh * 256 + (tid + 64) * 2 + 0];
+        Q1 += red[hh * 256 + (tid + 64) * 2 + 1];
+      }
+      const double f = a.dx * a.dy / a.scale;
+      a.V[2 * k] = ((double)P1 - (double)Q1) * f;
+      a.V[2 * k + 1] = -((double)P2 + (double)Q2) * f;
+    }
+  }
+  if (!ok && tid == 0) {
+    atomicCAS(a.status, 0, (int)BH_ERR_TIMEOUT);
+    // let any MMAs still in flight finish (bounded) before freeing TMEM
+    for (int s = 0; s < kStages; ++s)
+      if (use[s] > 0) mbar_wait(&bar_mma[s], (use[s] - 1) & 1);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+}  // namespace bhrt
+
+using namespace bhrt;
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes) {
+  if (!cam || !bytes || cam->nx < 1 || cam->ny < 1) return BH_ERR_INVALID_ARG;
+  int64_t nxp = ((int64_t)cam->nx + kVisKC - 1) / kVisKC * kVisKC;
+  *bytes = a256(sizeof(int)) + a256((size_t)cam->ny * 3 * nxp * 2);
+  return BH_OK;
+}
+
+bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
+                          int32_t mode, double image_max, double* V, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  if (!I || !cam || K < 0 || (K > 0 && (!uv || !V)) || cam->nx < 1 || cam->ny < 1 ||
+      (mode != 0 && cam->nx > kVisMaxNx) ||
+      !(cam->x_max > cam->x_min) || !(cam->y_max > cam->y_min) || !(image_max > 0.0) ||
+      !std::isfinite(image_max))
+    return BH_ERR_INVALID_ARG;
+  if (mode == 0) return bh_visibilities_fp64(I, cam, uv, K, V, stream);
+  if (mode != 1 && mode != 2) return BH_ERR_INVALID_ARG;
+  if (K == 0) return BH_OK;
+  size_t need;
+  bh_visibilities_workspace_size(cam, &need);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
+    return BH_ERR_WORKSPACE;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return BH_ERR_CUDA;
+  VisArgs a;
+  a.uv = uv;
+  a.K = K;
+  a.nx = cam->nx;
+  a.ny = cam->ny;
+  a.nxp = (cam->nx + kVisKC - 1) / kVisKC * kVisKC;
+  a.x_min = cam->x_min;
+  a.y_min = cam->y_min;
+  a.dx = (cam->x_max - cam->x_min) / cam->nx;
+  a.dy = (cam->y_max - cam->y_min) / cam->ny;
+  a.scale = 1.0 / image_max;
+  a.fp16 = mode == 2;
+  a.V = V;
+  char* ws = static_cast<char*>(workspace);
+  a.status = reinterpret_cast<int*>(ws);
+  uint16_t* Bp = reinterpret_cast<uint16_t*>(ws + a256(sizeof(int)));
+  // TMA map of B': [ny rows][3 nxp] 16-bit, box 64 x 256, 128-byte swizzle
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  cuuint64_t dims[2] = {(cuuint64_t)3 * a.nxp, (cuuint64_t)a.ny};
+  cuuint64_t strides[1] = {(cuuint64_t)3 * a.nxp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kVisKC, 256u};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(&map, a.fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                   2, Bp, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return BH_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return BH_ERR_CUDA;
+  vis_prepare_image<<<1216, 256, 0, s>>>(I, a, Bp);
+  if (cudaFuncSetAttribute(vis_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kVisSmem) != cudaSuccess)
+    return BH_ERR_CUDA;
+  const int64_t grid = (K + kVisUV - 1) / kVisUV;
+  if (grid > 0x7fffffff) return BH_ERR_INVALID_ARG;
+  vis_tc_kernel<<<(unsigned)grid, kVisThreads, kVisSmem, s>>>(map, a);
+  return cudaGetLastError() == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+"""The C ABI library loads without a GPU, exports every function that
+include/bhrt.h declares, and its host-side parts (geometry, argument checks
+that return before any device work) behave; no device compute is called."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bhrt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(bh_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2605_05635_gb300 import bhrt
+    bhrt.lib()
+    return bhrt
+
+
+def test_library_exports_every_declared_function(B):
+    lib = B.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_host_geometry_matches_oracle(B, oracle):
+    for metric, kw, okw in [(0, {}, {}), (1, dict(lambda_E=0.1), dict(lam_E=0.1)),
+                            (2, dict(eta=0.02, lambda_c=10.0), dict(eta=0.02, lam_c=10.0))]:
+        for chi in (0.0, 0.5, 0.9, 0.98):
+            rp, ce, ri = B.host_geometry(B.Spacetime(metric=metric, chi=chi, **kw))
+            P = oracle.problem(metric=metric, chi=chi, **okw)
+            assert rp == pytest.approx(oracle.horizon(P), rel=1e-13)
+            assert ce == pytest.approx(oracle.extremal_spin(P)[0], rel=1e-8)
+            assert ri == pytest.approx(oracle.isco(P), rel=2e-7)
+
+
+def test_host_geometry_errors(B):
+    with pytest.raises(B.BHRTError) as e:
+        B.host_geometry(B.Spacetime(metric=0, chi=1.2))
+    assert e.value.code == 2
+    with pytest.raises(B.BHRTError) as e:
+        B.host_geometry(B.Spacetime(metric=1, chi=0.7, lambda_E=0.3))
+    assert e.value.code == 2
+
+
+def test_argument_errors_return_before_device_work(B):
+    """Validation happens on the host before anything is enqueued."""
+    lib = B.lib()
+    st = B.Spacetime(metric=0, chi=0.5)._c()
+    cam = B.Camera()._c()
+    em = B.Emission()._c()
+    it = B.Integrator()._c()
+    out = B._ImageOut()
+    ws = C.c_void_p(0)
+    # no workspace
+    code = lib.bh_trace_image(C.byref(st), C.byref(cam), C.byref(em), C.byref(it), C.byref(out),
+                              ws, 0, None)
+    assert code in (1, 4)  # outputs missing (1) or workspace missing (4)
+    bad = B.Spacetime(metric=0, chi=1.01)._c()
+    code = lib.bh_trace_points(C.byref(bad), C.byref(cam), C.byref(em), C.byref(it), 0, None,
+                               None, ws, 0, None)
+    assert code == 2
+    far = B.Camera(r_obs=5.0)._c()
+    code = lib.bh_trace_points(C.byref(st), C.byref(far), C.byref(em), C.byref(it), 0, None,
+                               None, ws, 0, None)
+    assert code == 3
+    badint = B.Integrator(precision=7)._c()
+    code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(em), C.byref(badint), 0,
+                               None, None, ws, 0, None)
+    assert code == 1
+    incl = B.Camera(incl=math.pi)._c()
+    code = lib.bh_trace_points(C.byref(st), C.byref(incl), C.byref(em), C.byref(it), 0, None,
+                               None, ws, 0, None)
+    assert code == 1
+
+
+def test_workspace_sizes(B):
+    cam = B.Camera(nx=64, ny=48, refine_levels=2)
+    n64 = B.workspace_bytes([cam], B.Integrator(precision=0))
+    nmx = B.workspace_bytes([cam], B.Integrator(precision=1))
+    assert nmx > n64 > 64 * 48 * 32
+    assert B.workspace_bytes([cam, cam], B.Integrator()) > n64
+    with pytest.raises(B.BHRTError):
+        B.workspace_bytes([cam, B.Camera(nx=32, ny=48, refine_levels=2)])
+
+
+def test_status_strings(B):
+    for code in range(9):
+        assert B.status_string(code)
