@@ -244,6 +244,24 @@ bh_status bh_diagnostics_workspace_size(const bh_camera* cam, size_t* bytes);
 bh_status bh_diagnostics(const float* I, const bh_camera* cam, double theta_g, double* out12,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* Same diagnostics without a caller workspace; the paper has no counterpart.
+ * For callers that cannot allocate device memory when they need the result
+ * (a host framework that owns all device memory through its own pool, a
+ * plugin that only receives its input and output buffers, a timed loop that
+ * must not call cudaMalloc): the reduction scratch is a fixed 256 KiB
+ * file-scope device array that every GPU loading the library holds until
+ * process exit.  The call allocates nothing.  The first call on each device
+ * looks the array's device address up (cudaGetSymbolAddress) and caches it,
+ * so make that first call before any stream capture.  All calls share the
+ * array: the histogram is cleared on every call, but calls whose work
+ * overlaps on the GPU (different streams, or different host threads on one
+ * device) race on it.  Images whose radial profile needs more scratch than
+ * the array holds are rejected
+ * with BH_ERR_WORKSPACE before anything is enqueued; for a square screen
+ * centred on the origin that is a side above about 20,000 pixels. */
+bh_status bh_diagnostics_noalloc(const float* I, const bh_camera* cam, double theta_g,
+                                 double* out12, void* stream);
+
 /* Visibilities of Eq. (108), FP64 direct sum: V_k = sum_ij I_ij
  * exp[-2 pi i (u_k X_i + v_k Y_j)] dX dY for K baselines uv[2k], uv[2k+1]
  * in cycles per M (device doubles); V[2k], V[2k+1] = Re, Im (device).

@@ -334,3 +334,55 @@ bh_status bh_visibilities_fp64(const float* I, const bh_camera* cam, const doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Diagnostics without caller-provided scratch.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// diagnostics: code running inside a host framework that owns every device
+// allocation through its own pool, plugins that are handed only input and
+// output buffers, or loops that must not call cudaMalloc/cudaFree for timing
+// reasons.  For them the scratch of the two-pass reduction (block partials
+// and the radial-profile histogram) lives in a fixed file-scope device array,
+// kNoAllocScratchBytes long, which every GPU that loads this library keeps
+// until the process exits.  The host needs the array's device address: it is
+// looked up once per device with cudaGetSymbolAddress (the host-side symbol
+// is only a stand-in) and cached.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 256 * 1024;
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_diag_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+void* g_scratch_addr[kNoAllocMaxDevices];
+int g_scratch_ready[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device (nullptr on
+// failure).  The first call on a device does the lookup.
+void* noalloc_scratch() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return nullptr;
+  if (__atomic_load_n(&g_scratch_ready[dev], __ATOMIC_ACQUIRE)) return g_scratch_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_diag_scratch) != cudaSuccess || !p) return nullptr;
+  g_scratch_addr[dev] = p;
+  __atomic_store_n(&g_scratch_ready[dev], 1, __ATOMIC_RELEASE);
+  return p;
+}
+
+}  // namespace
+
+extern "C" bh_status bh_diagnostics_noalloc(const float* I, const bh_camera* cam, double theta_g,
+                                            double* out12, void* stream) {
+  DiagGeom g;
+  if (!I || !out12 || !geom_from(cam, theta_g, g)) return BH_ERR_INVALID_ARG;
+  if (diag_ws_layout(g, nullptr, nullptr) > kNoAllocScratchBytes) return BH_ERR_WORKSPACE;
+  void* scratch = noalloc_scratch();
+  if (!scratch) return BH_ERR_CUDA;
+  return bh_diagnostics(I, cam, theta_g, out12, scratch, kNoAllocScratchBytes, stream);
+}
