@@ -88,8 +88,10 @@ typedef struct {
   int32_t nx, ny;          /* base resolution, 1 .. 16384 each             */
   int32_t refine_levels;   /* adaptive 4x4 refinement depth, 0 .. 3        */
   int32_t reserved;        /* must be 0                                    */
-  int64_t refine_capacity; /* max cells per refinement level per call;
-                              0 selects max(16 * nx * ny * n_images, 65536) */
+  int64_t refine_capacity; /* max cells per refinement level per call; 0
+                              selects, per level L = 1, 2, 3, room for
+                              min(16^L, max(4 / 12 / 24, 2^22 / base pixels))
+                              cells per base pixel                          */
 } bh_camera;
 
 /* Emission (Sec. 5.1, Eqs. 83-87).  The thin-disk path evaluates j on the
@@ -227,6 +229,20 @@ bh_status bh_plan_set_timing(bh_plan plan, int32_t enable);
 bh_status bh_plan_stats(bh_plan plan, void* stream, bh_run_stats* out);
 bh_status bh_plan_destroy(bh_plan plan);
 
+/* Autotuner: runs the plan once per candidate launch shape of the persistent
+ * trace kernel (and of the FP64 pass of the mixed path), timing the trace
+ * kernels with CUDA events, and keeps the fastest shape for later launches
+ * (any captured graph is discarded and re-captured on the next graph launch).
+ * Synchronises the stream; outputs hold the last candidate's (identical)
+ * results. */
+typedef struct {
+  int32_t candidates;      /* shapes tried                                    */
+  int32_t blocks[2];       /* chosen grid: [0] main trace kernel, [1] FP64 pass */
+  int32_t threads[2];      /* chosen block size                               */
+  double best_ms[2];       /* trace time of the whole launch with the choice  */
+} bh_tune_report;
+bh_status bh_plan_autotune(bh_plan plan, void* stream, bh_tune_report* report);
+
 /* ---------------------------------------------------------------------- */
 /* Image diagnostics of Sec. 6.2-6.3 from a traced intensity plane I
  * (device float [ny][nx], screen geometry from cam).  out12 (device,
@@ -285,6 +301,34 @@ bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes);
 bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
                           int32_t mode, double image_max, double* V, void* workspace,
                           size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Gradients by a hand-written discrete adjoint of the FP64 image path.
+ * Loss: L = sum_p dL_dI[p] I[p] + sum_m dL_ddiag[m] D_m with
+ *   D = (C (Eq. 94), A_LR (Eq. 99), rho_peak, |V_k|/|V(0,0)| for the 8
+ *        baselines uv8 (Eq. 109)),
+ * where rho_peak is the vertex of the parabola through the origin-centred
+ * profile's peak bin and its two neighbours (a differentiable reading of
+ * Eq. 105's bin-centre peak).  grad10 (host) receives dL/d(chi, theta_o,
+ * halo1, halo2, j0, p, R_s, sigma_in, sigma_out, R_out); halo1 = lambda_E
+ * (Einasto) or eta (cored-NFW), halo2 = lambda_c (cored-NFW); unused halo
+ * entries are 0.  The derivative is that of the algorithm with its adaptive
+ * decisions frozen (accepted step sizes, refinement pattern, trusted
+ * crossings, termination step); R_in = r_ISCO or R_+ + dR_in is
+ * differentiated implicitly; the capture radius is held fixed.
+ * The forward pass runs in FP64 whatever integ->precision says.  Each ray
+ * is replayed with a checkpoint every 64 accepted steps; a ray needing more
+ * than 4096 accepted steps or 32 crossings returns BH_ERR_WORKSPACE.
+ * dL_dI (device float [ny][nx]), dL_ddiag (host, 11) and uv8 (host, 8x2
+ * cycles/M) may be NULL; diag11 (host) receives D; image_out (device float
+ * [ny][nx]) the forward intensity.  Synchronous: returns when grad10 is
+ * written.  Needs bh_backward_workspace_size bytes (256-byte aligned). */
+bh_status bh_backward_workspace_size(const bh_camera* cam, size_t* bytes);
+bh_status bh_trace_backward(const bh_spacetime* st, const bh_camera* cam, const bh_emission* em,
+                            const bh_integrator* integ, const float* dL_dI,
+                            const double* dL_ddiag, const double* uv8, double* grad10,
+                            double* diag11, float* image_out, void* workspace,
+                            size_t workspace_bytes, void* stream);
 
 /* Device status word of the last call that used this workspace (blocking
  * copy; call after synchronising the stream). */

@@ -129,6 +129,12 @@ def _load():
         lib.orc_trace_pixels.argtypes = [P, C.c_int64, C.POINTER(C.c_int32), D,
                                          C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
         lib.orc_trace_pixels.restype = C.c_int
+        lib.orc_trace_points_record.argtypes = [P, C.c_int64, D, C.POINTER(Ray), D, C.c_int,
+                                                C.POINTER(C.c_int32)]
+        lib.orc_trace_points_record.restype = C.c_int
+        lib.orc_trace_points_frozen.argtypes = [P, C.c_int64, D, D, C.c_int,
+                                                C.POINTER(C.c_int32), C.POINTER(Ray)]
+        lib.orc_trace_points_frozen.restype = C.c_int
         _lib = lib
         return lib
 
@@ -356,3 +362,41 @@ def trace_pixels(P: Problem, ij) -> dict:
     if rc:
         raise ValueError(f"oracle trace_pixels failed (code {rc})")
     return dict(val=val[:n], level=lev[:n], rays=nr[:n])
+
+
+def _rays_to_numpy(rays, n):
+    dt = np.dtype([(f, np.int32) if t is C.c_int32 else
+                   ((f, np.float64, (3,)) if hasattr(t, "_length_") else (f, np.float64))
+                   for f, t in Ray._fields_])
+    return np.frombuffer(bytes(rays), dtype=dt, count=n).copy()
+
+
+def trace_points_record(P: Problem, xy, hcap: int = 20000):
+    """Trace points and record each ray's accepted step sizes; returns
+    (records, hbuf [n, hcap], counts [n])."""
+    xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
+    n = xy.shape[0]
+    rays = (Ray * max(n, 1))()
+    hbuf = np.zeros((max(n, 1), hcap))
+    counts = np.zeros(max(n, 1), np.int32)
+    rc = _load().orc_trace_points_record(C.byref(P), n, _dp(xy), rays, _dp(hbuf), hcap,
+                                         counts.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc:
+        raise ValueError(f"oracle geometry setup failed (code {rc})")
+    if np.any(counts[:n] > hcap):
+        raise ValueError("step record buffer too small")
+    return _rays_to_numpy(rays, n), hbuf[:n], counts[:n]
+
+
+def trace_points_frozen(P: Problem, xy, hbuf, counts):
+    """Replay rays along recorded step sequences (no error control)."""
+    xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
+    n = xy.shape[0]
+    hbuf = np.ascontiguousarray(hbuf, dtype=np.float64)
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    rays = (Ray * max(n, 1))()
+    rc = _load().orc_trace_points_frozen(C.byref(P), n, _dp(xy), _dp(hbuf), hbuf.shape[1],
+                                         counts.ctypes.data_as(C.POINTER(C.c_int32)), rays)
+    if rc:
+        raise ValueError(f"oracle geometry setup failed (code {rc})")
+    return _rays_to_numpy(rays, n)

@@ -616,9 +616,17 @@ int orc_geometry_setup(const orc_problem* P, orc_geom* G) {
   return 0;
 }
 
-/* Integrate one backward ray from screen point (X, Y). */
-int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y,
-                  orc_ray* out) {
+/* Integrate one backward ray from screen point (X, Y).
+ * Optional instrumentation for gradient checks (test use):
+ *   hrec != NULL: the accepted step sizes are written to hrec[0..hcap) and
+ *                 their number to *nrec;
+ *   hplay != NULL: "frozen" replay of nplay accepted steps of the given sizes
+ *                 (no error control, no early termination): the map from
+ *                 parameters to results along a fixed step sequence, whose
+ *                 finite differences are smooth. */
+static int orc_trace_ray_core(const orc_problem* P, const orc_geom* G, double X, double Y,
+                              orc_ray* out, double* hrec, int hcap, int* nrec,
+                              const double* hplay, int nplay) {
   memset(out, 0, sizeof(*out));
   out->near_thdot = INFINITY;
   out->near_dlam = INFINITY;
@@ -640,17 +648,24 @@ int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y,
   const double half_pi = 0.5 * M_PI;
   out->status = 2;
 
+  if (nrec) *nrec = 0;
   for (int it = 0; it < P->max_steps; ++it) {
+    if (hplay) {
+      if (out->n_accept >= nplay) break;
+      h = hplay[out->n_accept];
+    }
     int bad = orc_dp5_trial(orc_geo_rhs, orc_geo_valid, &ctx, 6, y, h, k, y1, err);
-    if (bad) { h *= 0.5; rejected = 1; out->n_reject++; continue; }
+    if (bad && !hplay) { h *= 0.5; rejected = 1; out->n_reject++; continue; }
     double e = orc_err_norm(6, y, y1, err, P->rtol, P->atol);
-    if (!(e <= 1.0)) {
+    if (!hplay && !(e <= 1.0)) {
       h *= orc_step_factor(e, 1);
       rejected = 1;
       out->n_reject++;
       continue;
     }
+    if (hrec && out->n_accept < hcap) hrec[out->n_accept] = h;
     out->n_accept++;
+    if (nrec) *nrec = out->n_accept;
     /* Equatorial crossing test on the accepted step (Sec. 3.3, Sec. 4.2). */
     double s0 = y[2] - half_pi, s1 = y1[2] - half_pi;
     if ((s0 > 0.0 && s1 <= 0.0) || (s0 < 0.0 && s1 >= 0.0)) {
@@ -670,6 +685,10 @@ int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y,
       double yc[6];
       orc_dense(6, y, y1, h, k, sig, yc);
       double Rc = yc[1];
+      /* Reading: events count only inside the integration domain
+       * R_cap <= R <= R_esc, so the final step's overshoot past a
+       * termination radius cannot add a crossing. */
+      int in_domain = Rc >= G->R_cap && Rc <= G->R_esc;
       double Sig = Rc * Rc + P->chi * P->chi * cos(yc[2]) * cos(yc[2]);
       double thdot = yc[5] / Sig;                  /* Eq. (60) */
       double lamc = lam + sig * h;
@@ -679,7 +698,7 @@ int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y,
         double rl = fabs((lamc - lam_last) / P->dlambda_min - 1.0);
         if (rl < out->near_dlam) out->near_dlam = rl;
       }
-      int trusted = fabs(thdot) >= P->thetadot_min &&
+      int trusted = in_domain && fabs(thdot) >= P->thetadot_min &&
                     (!have_trusted || lamc - lam_last >= P->dlambda_min);
       if (trusted) {
         int n = out->ncross;
@@ -730,6 +749,7 @@ int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y,
       if (hd > out->h_drift) out->h_drift = hd;
     }
     if (y[1] < out->R_min) out->R_min = y[1];
+    if (hplay) continue;
     if (y[1] < G->R_cap) { out->status = 1; break; }     /* Eq. (75) */
     if (y[1] > G->R_esc) { out->status = 0; break; }     /* escape, Sec. 3.3 */
     h *= orc_step_factor(e, rejected);
@@ -738,6 +758,41 @@ int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y,
   out->R_final = y[1];
   out->lam_final = lam;
   out->K_final = orc_carter(P, E, ell, y[2], y[5]);
+  return 0;
+}
+
+int orc_trace_ray(const orc_problem* P, const orc_geom* G, double X, double Y, orc_ray* out) {
+  return orc_trace_ray_core(P, G, X, Y, out, NULL, 0, NULL, NULL, 0);
+}
+
+/* Points with their accepted step sequences recorded (hbuf[i*hcap ...]). */
+int orc_trace_points_record(const orc_problem* P, int64_t n, const double* xy, orc_ray* out,
+                            double* hbuf, int hcap, int32_t* counts) {
+  orc_geom G;
+  int rc = orc_geometry_setup(P, &G);
+  if (rc) return rc;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    int nr = 0;
+    orc_trace_ray_core(P, &G, xy[2 * i], xy[2 * i + 1], &out[i], hbuf + i * (int64_t)hcap, hcap,
+                       &nr, NULL, 0);
+    counts[i] = nr;
+  }
+  return 0;
+}
+
+/* Points replayed along given step sequences (frozen). */
+int orc_trace_points_frozen(const orc_problem* P, int64_t n, const double* xy,
+                            const double* hbuf, int hcap, const int32_t* counts, orc_ray* out) {
+  orc_geom G;
+  int rc = orc_geometry_setup(P, &G);
+  if (rc) return rc;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    int np = counts[i] < hcap ? counts[i] : hcap;
+    orc_trace_ray_core(P, &G, xy[2 * i], xy[2 * i + 1], &out[i], NULL, 0, NULL,
+                       hbuf + i * (int64_t)hcap, np);
+  }
   return 0;
 }
 

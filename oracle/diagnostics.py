@@ -50,7 +50,8 @@ def diagnostics(I, x_min, x_max, y_min, y_max, theta_g=1.0) -> dict:
     w_img = math.sqrt(_fsum((rho - rho_bar) ** 2 * I) * dA / F)         # Eq. (98)
     FR = _fsum(I[XX > Xc]) * dA                                         # Eq. (100)
     FL = _fsum(I[XX < Xc]) * dA
-    A_LR = (FR - FL) / (FR + FL)                                        # Eq. (99)
+    # Eq. (99); undefined (nan) when all flux sits on the centroid column
+    A_LR = (FR - FL) / (FR + FL) if FR + FL != 0.0 else math.nan
     pos = I[I > 0]
     P = float(I.max()) / (_fsum(pos) / pos.size)                        # Eq. (101)
     rho0 = np.sqrt(XX ** 2 + YY ** 2)                                   # Eq. (105)
@@ -79,3 +80,28 @@ def relative_change(Q, Q_kerr):
 def angular_scale(d, theta_g):
     """theta = d theta_g, Eq. (104)."""
     return d * theta_g
+
+
+def rho_peak_smooth(I, x_min, x_max, y_min, y_max):
+    """Differentiable reading of rho_peak (Eq. 105): the vertex of the parabola
+    through the mean intensities of the argmax bin and its two neighbours,
+    (b + 1/2 + delta) dX with delta = (m_- - m_+) / (2 (m_- - 2 m_0 + m_+));
+    delta = 0 at the ends of the profile or for a flat triple."""
+    I = np.asarray(I, dtype=np.float64)
+    ny, nx = I.shape
+    X, Y, dx, dy = screen_centres(nx, ny, x_min, x_max, y_min, y_max)
+    XX, YY = np.meshgrid(X, Y)
+    b = np.floor(np.sqrt(XX ** 2 + YY ** 2) / dx).astype(np.int64)
+    means = {}
+    for k in range(int(b.max()) + 1):
+        sel = I[b == k]
+        if sel.size:
+            means[k] = _fsum(sel) / sel.size
+    best = max(sorted(means), key=lambda k: (means[k], -k))
+    delta = 0.0
+    if best - 1 in means and best + 1 in means:
+        mm, m0, mp = means[best - 1], means[best], means[best + 1]
+        D = mm - 2.0 * m0 + mp
+        if D != 0.0:
+            delta = 0.5 * (mm - mp) / D
+    return (best + 0.5 + delta) * dx

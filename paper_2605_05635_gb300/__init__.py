@@ -3,6 +3,8 @@
 The compute path is the CUDA library ``libbhrt.so`` (C ABI in
 ``include/bhrt.h``); :mod:`.bhrt` is the Python binding.
 """
-from .bhrt import (CNFW, EINASTO, FP64, KERR, MIXED, BHRTError, Camera, Emission,  # noqa: F401
-                   Integrator, Plan, Spacetime, from_flat, host_geometry, lib, trace_batch,
-                   trace_image, trace_points)
+from .bhrt import (CNFW, DIAG_NAMES, EINASTO, FP64, KERR, MIXED, VIS_BF16,  # noqa: F401
+                   VIS_FP16, VIS_FP64, BHRTError, Camera, Emission, Integrator, Plan, Spacetime,
+                   diagnostics, from_flat, host_geometry, lib, trace_batch, trace_image,
+                   trace_points, visibilities, visibilities_fp64, trace_backward, BHRender,
+                   GRAD_NAMES, LOSS_DIAG_NAMES)

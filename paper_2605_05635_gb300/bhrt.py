@@ -93,6 +93,11 @@ class RunStats(C.Structure):
         return d
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("candidates", C.c_int32), ("blocks", C.c_int32 * 2),
+                ("threads", C.c_int32 * 2), ("best_ms", C.c_double * 2)]
+
+
 # ----------------------------------------------------------- user parameters
 @dataclasses.dataclass
 class Spacetime:
@@ -218,6 +223,8 @@ def lib():
         L.bh_plan_set_timing.argtypes = [C.c_void_p, C.c_int32]
         L.bh_plan_stats.argtypes = [C.c_void_p, C.c_void_p, P(RunStats)]
         L.bh_plan_destroy.argtypes = [C.c_void_p]
+        L.bh_plan_autotune.argtypes = [C.c_void_p, C.c_void_p, P(TuneReport)]
+        L.bh_plan_autotune.restype = C.c_int
         L.bh_diagnostics_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
         L.bh_diagnostics.argtypes = [C.c_void_p, P(_Camera), C.c_double, C.c_void_p, C.c_void_p,
                                      C.c_size_t, C.c_void_p]
@@ -226,6 +233,13 @@ def lib():
         L.bh_visibilities_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
         L.bh_visibilities.argtypes = [C.c_void_p, P(_Camera), C.c_void_p, C.c_int64, C.c_int32,
                                       C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.bh_backward_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
+        L.bh_trace_backward.argtypes = [P(_Spacetime), P(_Camera), P(_Emission), P(_Integrator),
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                        C.c_void_p]
+        L.bh_backward_workspace_size.restype = C.c_int
+        L.bh_trace_backward.restype = C.c_int
         for fn in ("bh_diagnostics_workspace_size", "bh_diagnostics", "bh_visibilities_fp64",
                    "bh_visibilities_workspace_size", "bh_visibilities"):
             getattr(L, fn).restype = C.c_int
@@ -398,6 +412,13 @@ class Plan:
         _check(lib().bh_plan_launch(self._h, int(use_graph), _stream_ptr(stream)),
                "bh_plan_launch")
 
+    def autotune(self, stream=None) -> dict:
+        rep = TuneReport()
+        _check(lib().bh_plan_autotune(self._h, _stream_ptr(stream), C.byref(rep)),
+               "bh_plan_autotune")
+        return dict(candidates=rep.candidates, blocks=list(rep.blocks),
+                    threads=list(rep.threads), best_ms=list(rep.best_ms))
+
     def set_timing(self, enable: bool):
         _check(lib().bh_plan_set_timing(self._h, int(enable)), "bh_plan_set_timing")
 
@@ -485,3 +506,78 @@ def visibilities(I: torch.Tensor, cam: Camera, uv: torch.Tensor, mode: int = VIS
     if check and mode != VIS_FP64:
         _check(lib().bh_workspace_status(C.c_void_p(workspace.data_ptr()), sp), "device status")
     return torch.view_as_complex(out)
+
+
+GRAD_NAMES = ["chi", "incl", "halo1", "halo2", "j0", "p", "R_s", "sigma_in", "sigma_out", "R_out"]
+LOSS_DIAG_NAMES = ["C", "A_LR", "rho_peak"] + [f"vis{k}" for k in range(8)]
+
+
+def trace_backward(st: Spacetime, cam: Camera, em: Emission, integ: Integrator,
+                   dL_dI: Optional[torch.Tensor] = None, dL_ddiag=None, uv8=None, device=None,
+                   stream=None):
+    """Gradient of L = sum dL_dI * I + sum dL_ddiag * D by the discrete adjoint.
+    Returns (grad [10] numpy, diag [11] numpy, forward image tensor)."""
+    import numpy as np
+
+    device = _need_cuda(device)
+    nb = C.c_size_t(0)
+    _check(lib().bh_backward_workspace_size(C.byref(cam._c()), C.byref(nb)),
+           "bh_backward_workspace_size")
+    ws = _aligned_workspace(nb.value, device)
+    grad = np.zeros(10)
+    diag = np.zeros(11)
+    img = torch.empty(cam.ny, cam.nx, dtype=torch.float32, device=device)
+    dd = None if dL_ddiag is None else np.ascontiguousarray(dL_ddiag, dtype=np.float64)
+    uv = None if uv8 is None else np.ascontiguousarray(np.asarray(uv8).reshape(8, 2),
+                                                        dtype=np.float64)
+    dli = None
+    if dL_dI is not None:
+        dli = dL_dI.to(device=device, dtype=torch.float32).contiguous()
+    ptr = lambda a: C.c_void_p(a.ctypes.data) if a is not None else C.c_void_p(0)
+    code = lib().bh_trace_backward(
+        C.byref(st._c()), C.byref(cam._c()), C.byref(em._c()), C.byref(integ._c()),
+        C.c_void_p(dli.data_ptr()) if dli is not None else C.c_void_p(0), ptr(dd), ptr(uv),
+        ptr(grad), ptr(diag), C.c_void_p(img.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream_ptr(stream))
+    _check(code, "bh_trace_backward")
+    return grad, diag, img
+
+
+class BHRender(torch.autograd.Function):
+    """Differentiable render: forward = FP64 image of the given parameters,
+    backward = the library's discrete adjoint.  params is a float64 tensor
+    (chi, incl, halo1, halo2, j0, p, R_s, sigma_in, sigma_out, R_out); the
+    remaining settings come from the template structs."""
+
+    @staticmethod
+    def forward(ctx, params, st: Spacetime, cam: Camera, em: Emission, integ: Integrator):
+        st2, em2 = _apply_params(params, st, em)
+        cam2 = dataclasses.replace(cam, incl=float(params[1]))
+        out = trace_image(st2, cam2, em2, dataclasses.replace(integ, precision=FP64))
+        ctx.save_for_backward(params)
+        ctx.cfg = (st, cam, em, integ)
+        return out["I"]
+
+    @staticmethod
+    def backward(ctx, gI):
+        (params,) = ctx.saved_tensors
+        st, cam, em, integ = ctx.cfg
+        st2, em2 = _apply_params(params, st, em)
+        cam2 = dataclasses.replace(cam, incl=float(params[1]))
+        grad, _, _ = trace_backward(st2, cam2, em2, integ, dL_dI=gI)
+        return torch.as_tensor(grad, dtype=params.dtype, device=params.device), None, None, \
+            None, None
+
+
+def _apply_params(params, st: Spacetime, em: Emission):
+    p = [float(x) for x in params]
+    kw = dict(chi=p[0])
+    if st.metric == EINASTO:
+        kw["lambda_E"] = p[2]
+    elif st.metric == CNFW:
+        kw["eta"] = p[2]
+        kw["lambda_c"] = p[3]
+    st2 = dataclasses.replace(st, **kw)
+    em2 = dataclasses.replace(em, j0=p[4], p=p[5], R_s=p[6], sigma_in=p[7], sigma_out=p[8],
+                              R_out=p[9])
+    return st2, em2

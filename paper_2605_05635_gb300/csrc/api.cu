@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include "adjoint.h"
+#include "dual.cuh"
 #include "internal.h"
 
 using namespace bhrt;
@@ -264,7 +266,11 @@ struct Layout {
   size_t total;
 };
 
-Layout make_layout(int n, int64_t npix, int levels, int64_t cap, int precision) {
+struct Caps {
+  int64_t c[kMaxLevels + 1];  // cells per refinement level (index 1..3)
+};
+
+Layout make_layout(int n, int64_t npix, int levels, const Caps& caps, int precision) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -280,18 +286,21 @@ Layout make_layout(int n, int64_t npix, int levels, int64_t cap, int precision) 
   L.base_cls = take(sizeof(uint16_t) * nb);
   L.base_child = take(sizeof(int32_t) * nb);
   L.base_depth = take(nb);
+  int64_t maxcap = nb;
   for (int l = 1; l <= levels; ++l) {
+    const int64_t cap = caps.c[l];
     L.lv_key[l] = take(sizeof(uint64_t) * cap);
     L.lv_img[l] = take(sizeof(uint32_t) * cap);
     L.lv_I[l] = take(sizeof(double) * 4 * cap);
     L.lv_cls[l] = take(sizeof(uint16_t) * cap);
     L.lv_child[l] = take(sizeof(int32_t) * cap);
     L.lv_depth[l] = take(cap);
+    if (cap > maxcap) maxcap = cap;
   }
   L.spill_cap = 0;
   L.spill[0] = L.spill[1] = 0;
   if (precision == 1) {
-    L.spill_cap = levels > 0 && cap > nb ? cap : nb;
+    L.spill_cap = maxcap;
     L.spill[0] = take(spill_record_bytes() * L.spill_cap);
     L.spill[1] = take(spill_record_bytes() * L.spill_cap);
   }
@@ -299,12 +308,31 @@ Layout make_layout(int n, int64_t npix, int levels, int64_t cap, int precision) 
   return L;
 }
 
-int64_t default_cap(int n, const bh_camera& c) {
-  int64_t cap = c.refine_capacity > 0 ? c.refine_capacity : 16 * (int64_t)c.nx * c.ny * n;
-  if (c.refine_capacity == 0 && cap < 65536) cap = 65536;
-  cap = (cap + 15) & ~int64_t(15);
-  if (cap > (int64_t(1) << 30)) cap = int64_t(1) << 30;  // int32 child indices
-  return cap;
+// Cells per refinement level.  A caller-given capacity applies to every
+// level; otherwise level L holds min(16^L, max(f_L, 2^22 / (n nx ny))) cells
+// per base pixel with f = 4, 12, 24: room for 25 % of the base pixels to be
+// refined and the boundary to keep growing x3 and x2 per level, and for
+// every cell of a coarse screen to be refined.
+Caps default_caps(int n, const bh_camera& c) {
+  Caps k{};
+  const int64_t nb = (int64_t)c.nx * c.ny * n;
+  const int64_t f[kMaxLevels + 1] = {0, 4, 12, 24};
+  int64_t full = nb;
+  for (int l = 1; l <= kMaxLevels; ++l) {
+    full = full > (int64_t(1) << 40) ? full : full * 16;
+    int64_t cap;
+    if (c.refine_capacity > 0) {
+      cap = c.refine_capacity;
+    } else {
+      cap = f[l] * nb;
+      if (cap < (int64_t(1) << 22)) cap = int64_t(1) << 22;
+      if (cap > full) cap = full;
+    }
+    cap = (cap + 15) & ~int64_t(15);
+    if (cap > (int64_t(1) << 30)) cap = int64_t(1) << 30;  // int32 child indices
+    k.c[l] = cap;
+  }
+  return k;
 }
 
 int num_sms() {
@@ -319,7 +347,8 @@ int num_sms() {
 // ------------------------------------------------------------------- plan
 struct bh_plan_s {
   int n = 0, levels = 0, precision = 0;
-  int64_t npix = 0, cap = 0;
+  int64_t npix = 0;
+  Caps caps{};
   std::vector<ImgParams> ip;
   std::vector<OutPtrs> out;
   char* ws = nullptr;
@@ -357,7 +386,7 @@ bh_status plan_build(int32_t n, const bh_spacetime* st, const bh_camera* cam,
   p.levels = cam[0].refine_levels;
   p.precision = integ[0].precision;
   p.npix = (int64_t)cam[0].nx * cam[0].ny;
-  p.cap = default_cap(n, cam[0]);
+  p.caps = default_caps(n, cam[0]);
   p.ip.resize(n);
   p.out.resize(n);
   double budget = 0.0;
@@ -385,7 +414,7 @@ bh_status plan_build(int32_t n, const bh_spacetime* st, const bh_camera* cam,
     if (integ[i].time_budget_s > budget) budget = integ[i].time_budget_s;
   }
   p.budget_ns = (unsigned long long)(budget * 1e9);
-  p.L = make_layout(n, p.npix, p.levels, p.cap, p.precision);
+  p.L = make_layout(n, p.npix, p.levels, p.caps, p.precision);
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < p.L.total)
     return BH_ERR_WORKSPACE;
   p.ws = static_cast<char*>(ws);
@@ -420,7 +449,7 @@ TraceArgs trace_args(const bh_plan_s& p, int level) {
     a.lv.cls = reinterpret_cast<uint16_t*>(p.ws + p.L.lv_cls[level]);
     a.lv.child = reinterpret_cast<int32_t*>(p.ws + p.L.lv_child[level]);
     a.lv.depth = reinterpret_cast<uint8_t*>(p.ws + p.L.lv_depth[level]);
-    a.lv.cap = p.cap;
+    a.lv.cap = p.caps.c[level];
   }
   return a;
 }
@@ -566,7 +595,7 @@ bh_status bh_workspace_size(int32_t n, const bh_camera* cameras, const bh_integr
       return BH_ERR_INVALID_ARG;
   int precision = integ ? integ->precision : 0;
   if (precision < 0 || precision > kMaxPrecision) return BH_ERR_INVALID_ARG;
-  *bytes = make_layout(n, (int64_t)c.nx * c.ny, c.refine_levels, default_cap(n, c), precision)
+  *bytes = make_layout(n, (int64_t)c.nx * c.ny, c.refine_levels, default_caps(n, c), precision)
                .total;
   return BH_OK;
 }
@@ -739,6 +768,66 @@ bh_status bh_plan_stats(bh_plan p, void* stream, bh_run_stats* out) {
   return BH_OK;
 }
 
+// Autotuner: times the whole launch (all levels, all precision passes) for
+// each candidate shape of the persistent trace kernel(s) and keeps the
+// fastest.  Candidates: 128-thread blocks at 1..occupancy blocks per SM and
+// 64-thread blocks at twice that, for the main kernel; the FP64 pass of the
+// mixed path is tuned afterwards the same way.
+bh_status bh_plan_autotune(bh_plan p, void* stream, bh_tune_report* rep) {
+  if (!p) return BH_ERR_INVALID_ARG;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const bool was_timing = p->timing;
+  if (bh_plan_set_timing(p, 1) != BH_OK) return BH_ERR_CUDA;
+  if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  const int sms = num_sms();
+  auto run_ms = [&](double& ms) -> bh_status {
+    bh_status s = enqueue(*p, cs);
+    if (s != BH_OK) return s;
+    bh_run_stats st;
+    s = bh_plan_stats(p, stream, &st);
+    if (s != BH_OK) return s;
+    if (st.status != BH_OK) return static_cast<bh_status>(st.status);
+    ms = 0.0;
+    for (int l = 0; l <= p->levels; ++l) ms += st.trace_ms[l];
+    return BH_OK;
+  };
+  int tried = 0;
+  for (int which = 0; which < (p->precision == 1 ? 2 : 1); ++which) {
+    LaunchShape& sh = which == 0 ? p->shape : p->shape64;
+    const int prec = which == 0 ? p->precision : 0;
+    const int occ = trace_default_blocks_per_sm(prec, 128);
+    LaunchShape cand[16];
+    int nc = 0;
+    for (int b = 1; b <= occ && nc < 12; ++b) cand[nc++] = LaunchShape{sms * b, 128};
+    cand[nc++] = LaunchShape{sms * 2 * occ, 64};
+    LaunchShape best = sh;
+    double best_ms = 1e300;
+    for (int c = 0; c < nc; ++c) {
+      sh = cand[c];
+      double ms;
+      bh_status s = run_ms(ms);
+      if (s != BH_OK) return s;
+      ++tried;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand[c];
+      }
+    }
+    sh = best;
+    if (rep) {
+      rep->best_ms[which] = best_ms;
+      rep->blocks[which] = best.blocks;
+      rep->threads[which] = best.threads;
+    }
+  }
+  if (rep) rep->candidates = tried;
+  p->timing = was_timing;
+  return BH_OK;
+}
+
 bh_status bh_plan_destroy(bh_plan p) {
   if (!p) return BH_OK;
   if (p->graph) cudaGraphExecDestroy(p->graph);
@@ -756,6 +845,325 @@ bh_status bh_workspace_status(const void* workspace, void* stream) {
     return BH_ERR_CUDA;
   if (cudaStreamSynchronize(cs) != cudaSuccess) return BH_ERR_CUDA;
   return static_cast<bh_status>(st);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ adjoint
+namespace {
+
+constexpr int kAdjThreads = 128;
+constexpr int kAdjBlocksPerSM = 2;
+constexpr int kAdjMaxCkpt = 64;  // 64 checkpoints x 64 steps = 4096 accepted steps per ray
+
+// Lapse H(R) for any scalar type: Kerr, Eq. (9) with halo1 = lambda_E,
+// Eq. (13) with halo1 = eta, halo2 = lambda_c.
+template <class T>
+T lapse_any(int metric, const T& R, const T& h1, const T& h2) {
+  using std::exp;
+  using std::log1p;
+  if (metric == BH_EINASTO) {
+    T e = exp(-R / h1);
+    return 1.0 - 2.0 / R + (2.0 / R + 2.0 / h1 + R / (h1 * h1)) * e;
+  }
+  if (metric == BH_CNFW) {
+    T S = h1 * h2 * (1.0 / (R + h2) - (2.0 / R) * log1p(R / h2));
+    return exp(S) - 2.0 / R;
+  }
+  return 1.0 - 2.0 / R;
+}
+
+// Prograde circular-orbit energy -u_T (Eqs. 90-91) with H' from a dual.
+double circ_energy(int metric, double R, double chi, double h1, double h2) {
+  Dual<1> Hd = lapse_any(metric, Dual<1>::var(R, 0), Dual<1>(h1), Dual<1>(h2));
+  const double H = Hd.v, dH = Hd.d[0], x2 = chi * chi;
+  const double den = 2.0 * R - x2 * dH, disc = 2.0 * R * dH;
+  const double W = (-chi * dH + std::sqrt(disc)) / den;
+  const double gtt = -H, gtp = -chi * (1.0 - H), gpp = R * R + x2 + x2 * (1.0 - H);
+  const double norm = -(gtt + 2.0 * W * gtp + W * W * gpp);
+  return -(gtt + W * gtp) / std::sqrt(norm);
+}
+
+// Derivatives of the ZAMO frame at the observer and of R_in with respect
+// to (chi, theta_o, halo1, halo2).
+AdjImg adjoint_constants(const bh_spacetime& s, const bh_camera& c, const bh_emission& e,
+                         const ImgParams& ip) {
+  using D4 = Dual<4>;
+  AdjImg aj;
+  std::memset(&aj, 0, sizeof(aj));
+  const bool ein = s.metric == BH_EINASTO, nfw = s.metric == BH_CNFW;
+  D4 chi = D4::var(s.chi, 0), th = D4::var(c.incl, 1);
+  D4 h1 = ein ? D4::var(s.lambda_E, 2) : (nfw ? D4::var(s.eta, 2) : D4(1.0));
+  D4 h2 = nfw ? D4::var(s.lambda_c, 3) : D4(1.0);
+  D4 R(c.r_obs);
+  D4 H = lapse_any(s.metric, R, h1, h2);
+  D4 cs = cos(th), sn = sin(th), s2 = sn * sn, x2 = chi * chi;
+  D4 Sig = R * R + x2 * cs * cs, F = R * R * (1.0 - H), D = R * R * H + x2;
+  D4 gtt = -(1.0 - F / Sig), gtp = -chi * F * s2 / Sig, grr = Sig / D, gthth = Sig;
+  D4 gpp = s2 * (R * R + x2 + x2 * F * s2 / Sig);
+  D4 w = -gtp / gpp;
+  D4 N = sqrt(-(gtt + 2.0 * w * gtp + w * w * gpp));
+  D4 sr = sqrt(grr), st = sqrt(gthth), sp = sqrt(gpp);
+  for (int k = 0; k < 4; ++k) {
+    aj.d_sqgrr[k] = sr.d[k];
+    aj.d_sqgth[k] = st.d[k];
+    aj.d_sqgph[k] = sp.d[k];
+    aj.d_N[k] = N.d[k];
+    aj.d_w[k] = w.d[k];
+  }
+  const double p1 = ein ? s.lambda_E : (nfw ? s.eta : 1.0), p2 = nfw ? s.lambda_c : 1.0;
+  if (e.r_in_mode == 1) {
+    // R_in = R_+ + dR_in: implicit derivative of Delta(R_+) = 0
+    using D5 = Dual<5>;
+    D5 Rp = D5::var(ip.r_plus, 0), ch = D5::var(s.chi, 1);
+    D5 q1 = (ein || nfw) ? D5::var(p1, 3) : D5(p1), q2 = nfw ? D5::var(p2, 4) : D5(p2);
+    D5 Dl = Rp * Rp * lapse_any(s.metric, Rp, q1, q2) + ch * ch;
+    for (int k = 0; k < 4; ++k) aj.d_Rin[k] = k == 1 ? 0.0 : -Dl.d[1 + k] / Dl.d[0];
+  } else {
+    // R_in = r_ISCO: dE/dR = 0, so dR/dq = -E_Rq / E_RR (central differences)
+    const double Ri = ip.R_in, dR = 1e-3;
+    auto ER = [&](double rr, double ch, double a1, double a2) {
+      return (circ_energy(s.metric, rr + dR, ch, a1, a2) -
+              circ_energy(s.metric, rr - dR, ch, a1, a2)) / (2.0 * dR);
+    };
+    const double ERR = (circ_energy(s.metric, Ri + dR, s.chi, p1, p2) -
+                        2.0 * circ_energy(s.metric, Ri, s.chi, p1, p2) +
+                        circ_energy(s.metric, Ri - dR, s.chi, p1, p2)) / (dR * dR);
+    const double base[4] = {s.chi, 0.0, p1, p2};
+    for (int k = 0; k < 4; ++k) {
+      if (k == 1 || (k >= 2 && !(ein || nfw)) || (k == 3 && !nfw)) continue;
+      double q[4] = {base[0], 0.0, base[2], base[3]};
+      const double eps = 1e-4 * std::fmax(std::fabs(base[k]), 1e-2);
+      q[k] = base[k] + eps;
+      const double up = ER(Ri, q[0], q[2], q[3]);
+      q[k] = base[k] - eps;
+      const double dn = ER(Ri, q[0], q[2], q[3]);
+      aj.d_Rin[k] = -((up - dn) / (2.0 * eps)) / ERR;
+    }
+  }
+  return aj;
+}
+
+struct BwdLayout {
+  Layout fwd;
+  size_t I, nc, st, G, mom, lr, hs, hc, uv, V, grad, head, status, ckpt, total;
+  int nbins, threads;
+};
+
+bool bwd_layout(const bh_camera& c, BwdLayout& B) {
+  if (c.nx < 1 || c.ny < 1 || c.refine_levels < 0 || c.refine_levels > kMaxLevels ||
+      !(c.x_max > c.x_min))
+    return false;
+  const int64_t npix = (int64_t)c.nx * c.ny;
+  B.fwd = make_layout(1, npix, c.refine_levels, default_caps(1, c), 0);
+  const double dx = (c.x_max - c.x_min) / c.nx;
+  const double ax = std::fmax(std::fabs(c.x_min), std::fabs(c.x_max));
+  const double ay = std::fmax(std::fabs(c.y_min), std::fabs(c.y_max));
+  B.nbins = (int)std::floor(std::sqrt(ax * ax + ay * ay) / dx) + 2;
+  B.threads = num_sms() * kAdjBlocksPerSM * kAdjThreads;
+  size_t o = B.fwd.total;
+  auto take = [&](size_t b) {
+    size_t at = o;
+    o = align256(o + b);
+    return at;
+  };
+  B.I = take(sizeof(float) * npix);
+  B.nc = take(npix);
+  B.st = take(npix);
+  B.G = take(sizeof(double) * npix);
+  B.mom = take(sizeof(double) * 3);
+  B.lr = take(sizeof(double) * 2);
+  B.hs = take(sizeof(double) * B.nbins);
+  B.hc = take(sizeof(unsigned long long) * B.nbins);
+  B.uv = take(sizeof(double) * 16);
+  B.V = take(sizeof(double) * 16);
+  B.grad = take(sizeof(double) * 10);
+  B.head = take(sizeof(unsigned long long));
+  B.status = take(sizeof(int));
+  B.ckpt = take(sizeof(Ckpt) * (size_t)B.threads * kAdjMaxCkpt);
+  B.total = o;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+bh_status bh_backward_workspace_size(const bh_camera* cam, size_t* bytes) {
+  BwdLayout B;
+  if (!cam || !bytes || !bwd_layout(*cam, B)) return BH_ERR_INVALID_ARG;
+  *bytes = B.total;
+  return BH_OK;
+}
+
+bh_status bh_trace_backward(const bh_spacetime* st, const bh_camera* cam, const bh_emission* em,
+                            const bh_integrator* integ, const float* dL_dI,
+                            const double* dL_ddiag, const double* uv8, double* grad10,
+                            double* diag11, float* image_out, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  if (!st || !cam || !em || !integ || !grad10) return BH_ERR_INVALID_ARG;
+  BwdLayout BL;
+  if (!bwd_layout(*cam, BL)) return BH_ERR_INVALID_ARG;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < BL.total)
+    return BH_ERR_WORKSPACE;
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  bh_integrator it64 = *integ;
+  it64.precision = 0;  // the adjoint differentiates the FP64 path
+  const int64_t npix = (int64_t)cam->nx * cam->ny;
+  float* I = reinterpret_cast<float*>(ws + BL.I);
+  bh_image_out out;
+  std::memset(&out, 0, sizeof(out));
+  out.I = I;
+  out.ncross = reinterpret_cast<uint8_t*>(ws + BL.nc);
+  out.status = reinterpret_cast<uint8_t*>(ws + BL.st);
+  // 1. forward image
+  bh_plan_s p;
+  bh_status s;
+  try {
+    s = plan_build(1, st, cam, em, &it64, &out, ws, BL.fwd.total, p);
+  } catch (const std::bad_alloc&) {
+    return BH_ERR_INVALID_ARG;
+  }
+  if (s != BH_OK) return s;
+  if ((s = upload(p, cs)) != BH_OK) return s;
+  if ((s = enqueue(p, cs)) != BH_OK) return s;
+  // 2. image statistics for the diagnostics terms
+  ImgAdj A;
+  std::memset(&A, 0, sizeof(A));
+  A.nx = cam->nx;
+  A.ny = cam->ny;
+  A.x_min = cam->x_min;
+  A.y_min = cam->y_min;
+  A.dx = (cam->x_max - cam->x_min) / cam->nx;
+  A.dy = (cam->y_max - cam->y_min) / cam->ny;
+  A.nbins = BL.nbins;
+  double* mom = reinterpret_cast<double*>(ws + BL.mom);
+  double* lr = reinterpret_cast<double*>(ws + BL.lr);
+  double* hs = reinterpret_cast<double*>(ws + BL.hs);
+  unsigned long long* hc = reinterpret_cast<unsigned long long*>(ws + BL.hc);
+  if (cudaMemsetAsync(ws + BL.mom, 0, BL.uv - BL.mom, cs) != cudaSuccess) return BH_ERR_CUDA;
+  if (launch_image_moments(I, A, mom, cs) != cudaSuccess) return BH_ERR_CUDA;
+  double hm[3];
+  if (cudaMemcpyAsync(hm, mom, sizeof(hm), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  A.S = hm[0];
+  A.Xc = hm[0] != 0.0 ? hm[1] / hm[0] : 0.0;
+  A.Yc = hm[0] != 0.0 ? hm[2] / hm[0] : 0.0;
+  A.C = std::sqrt(A.Xc * A.Xc + A.Yc * A.Yc);
+  if (launch_image_profile(I, A, lr, hs, hc, cs) != cudaSuccess) return BH_ERR_CUDA;
+  std::vector<double> hsv(BL.nbins);
+  std::vector<unsigned long long> hcv(BL.nbins);
+  double hlr[2];
+  if (cudaMemcpyAsync(hlr, lr, sizeof(hlr), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaMemcpyAsync(hsv.data(), hs, sizeof(double) * BL.nbins, cudaMemcpyDeviceToHost, cs) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(hcv.data(), hc, sizeof(unsigned long long) * BL.nbins,
+                      cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  A.FRs = hlr[0];
+  A.FLs = hlr[1];
+  const double A_LR = (A.FRs + A.FLs) != 0.0 ? (A.FRs - A.FLs) / (A.FRs + A.FLs) : 0.0;
+  // radial profile peak with a parabolic vertex through the argmax bin and
+  // its neighbours (differentiable reading of the bin-centre peak)
+  int bstar = -1;
+  double bv = 0.0;
+  for (int b = 0; b < BL.nbins; ++b) {
+    if (!hcv[b]) continue;
+    const double m = hsv[b] / (double)hcv[b];
+    if (bstar < 0 || m > bv) {
+      bv = m;
+      bstar = b;
+    }
+  }
+  double delta = 0.0;
+  A.bstar = bstar;
+  if (bstar > 0 && bstar + 1 < BL.nbins && hcv[bstar - 1] && hcv[bstar + 1]) {
+    const double mm = hsv[bstar - 1] / (double)hcv[bstar - 1], m0 = bv,
+                 mp = hsv[bstar + 1] / (double)hcv[bstar + 1];
+    const double Dd = mm - 2.0 * m0 + mp, Nn = 0.5 * (mm - mp);
+    if (Dd != 0.0) {
+      delta = Nn / Dd;
+      A.drho[0] = A.dx * (0.5 * Dd - Nn) / (Dd * Dd);
+      A.drho[1] = A.dx * (2.0 * Nn) / (Dd * Dd);
+      A.drho[2] = A.dx * (-0.5 * Dd - Nn) / (Dd * Dd);
+      for (int t = 0; t < 3; ++t) A.cnt[t] = (int)hcv[bstar - 1 + t];
+    }
+  }
+  const double rho_peak = (bstar + 0.5 + delta) * A.dx;
+  // visibility amplitudes at the given baselines
+  double hv[16] = {0};
+  const double dA = A.dx * A.dy;
+  A.V0 = A.S * dA;
+  if (uv8) {
+    std::memcpy(A.uv, uv8, sizeof(double) * 16);
+    if (cudaMemcpyAsync(ws + BL.uv, uv8, sizeof(double) * 16, cudaMemcpyHostToDevice, cs) !=
+        cudaSuccess)
+      return BH_ERR_CUDA;
+    s = bh_visibilities_fp64(I, cam, reinterpret_cast<double*>(ws + BL.uv), 8,
+                             reinterpret_cast<double*>(ws + BL.V), stream);
+    if (s != BH_OK) return s;
+    if (cudaMemcpyAsync(hv, ws + BL.V, sizeof(hv), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)
+      return BH_ERR_CUDA;
+  }
+  for (int k = 0; k < 8; ++k) {
+    A.Vre[k] = hv[2 * k];
+    A.Vim[k] = hv[2 * k + 1];
+    A.Vabs[k] = std::sqrt(hv[2 * k] * hv[2 * k] + hv[2 * k + 1] * hv[2 * k + 1]);
+  }
+  if (diag11) {
+    diag11[0] = A.C;
+    diag11[1] = A_LR;
+    diag11[2] = rho_peak;
+    for (int k = 0; k < 8; ++k) diag11[3 + k] = A.V0 != 0.0 ? A.Vabs[k] / A.V0 : 0.0;
+  }
+  // 3. dL/dI per pixel
+  A.dLdI = dL_dI;
+  if (dL_ddiag) {
+    A.cC = dL_ddiag[0];
+    A.cA = dL_ddiag[1];
+    A.cR = dL_ddiag[2];
+    for (int k = 0; k < 8; ++k) A.cV[k] = uv8 ? dL_ddiag[3 + k] : 0.0;
+  }
+  A.G = reinterpret_cast<double*>(ws + BL.G);
+  if (launch_pixel_adjoint(A, cs) != cudaSuccess) return BH_ERR_CUDA;
+  // 4. rays
+  AdjArgs J;
+  std::memset(&J, 0, sizeof(J));
+  RefineArgs ra = refine_args(p);
+  J.hdr = ra.hdr;
+  J.ip = ra.ip;
+  J.aj = adjoint_constants(*st, *cam, *em, p.ip[0]);
+  J.levels = p.levels;
+  J.npix = npix;
+  J.Gpix = A.G;
+  J.base_child = ra.base_child;
+  for (int l = 1; l <= kMaxLevels; ++l) J.lv[l] = ra.lv[l];
+  J.ckpt = reinterpret_cast<Ckpt*>(ws + BL.ckpt);
+  J.max_ckpt = kAdjMaxCkpt;
+  J.grad = reinterpret_cast<double*>(ws + BL.grad);
+  J.head = reinterpret_cast<unsigned long long*>(ws + BL.head);
+  J.status = reinterpret_cast<int*>(ws + BL.status);
+  if (cudaMemsetAsync(ws + BL.grad, 0, BL.ckpt - BL.grad, cs) != cudaSuccess) return BH_ERR_CUDA;
+  if (launch_adjoint(J, BL.threads / kAdjThreads, kAdjThreads, cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  int dstat = 0;
+  if (cudaMemcpyAsync(grad10, J.grad, sizeof(double) * 10, cudaMemcpyDeviceToHost, cs) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&dstat, J.status, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  if (image_out &&
+      cudaMemcpyAsync(image_out, I, sizeof(float) * npix, cudaMemcpyDeviceToDevice, cs) !=
+          cudaSuccess)
+    return BH_ERR_CUDA;
+  if (cudaStreamSynchronize(cs) != cudaSuccess) return BH_ERR_CUDA;
+  WsHeader h;
+  if (cudaMemcpy(&h, ra.hdr, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return BH_ERR_CUDA;
+  if (h.status != BH_OK) return static_cast<bh_status>(h.status);
+  return static_cast<bh_status>(dstat);
 }
 
 }  // extern "C"

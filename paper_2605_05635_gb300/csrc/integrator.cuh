@@ -33,6 +33,36 @@ __device__ constexpr DPTab kDP = {
      -10690763975.0 / 1880347072.0, 701980252875.0 / 199316789632.0,
      -1453857185.0 / 822651844.0, 69997945.0 / 29380423.0}};
 
+// The same tableau rounded to FP32 for the FP32 steps of the mixed path
+// (kept as literal floats so no FP64 conversion reaches the inner loop).
+struct DPTabF {
+  float a[7][6];
+  float b[7];
+  float e[7];
+  float d[7];
+};
+#define BH_F(x) static_cast<float>(x)
+__device__ constexpr DPTabF kDPf = {
+    {{0, 0, 0, 0, 0, 0},
+     {BH_F(1.0 / 5), 0, 0, 0, 0, 0},
+     {BH_F(3.0 / 40), BH_F(9.0 / 40), 0, 0, 0, 0},
+     {BH_F(44.0 / 45), BH_F(-56.0 / 15), BH_F(32.0 / 9), 0, 0, 0},
+     {BH_F(19372.0 / 6561), BH_F(-25360.0 / 2187), BH_F(64448.0 / 6561), BH_F(-212.0 / 729), 0,
+      0},
+     {BH_F(9017.0 / 3168), BH_F(-355.0 / 33), BH_F(46732.0 / 5247), BH_F(49.0 / 176),
+      BH_F(-5103.0 / 18656), 0},
+     {BH_F(35.0 / 384), 0, BH_F(500.0 / 1113), BH_F(125.0 / 192), BH_F(-2187.0 / 6784),
+      BH_F(11.0 / 84)}},
+    {BH_F(35.0 / 384), 0, BH_F(500.0 / 1113), BH_F(125.0 / 192), BH_F(-2187.0 / 6784),
+     BH_F(11.0 / 84), 0},
+    {BH_F(35.0 / 384 - 5179.0 / 57600), 0, BH_F(500.0 / 1113 - 7571.0 / 16695),
+     BH_F(125.0 / 192 - 393.0 / 640), BH_F(-2187.0 / 6784 + 92097.0 / 339200),
+     BH_F(11.0 / 84 - 187.0 / 2100), BH_F(-1.0 / 40)},
+    {BH_F(-12715105075.0 / 11282082432.0), 0, BH_F(87487479700.0 / 32700410799.0),
+     BH_F(-10690763975.0 / 1880347072.0), BH_F(701980252875.0 / 199316789632.0),
+     BH_F(-1453857185.0 / 822651844.0), BH_F(69997945.0 / 29380423.0)}};
+#undef BH_F
+
 constexpr double kHalfPi = 1.57079632679489661923;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;
@@ -154,7 +184,8 @@ static __device__ __noinline__ void handle_crossing(const ImgParams& ip, const M
   double Sig = yc[1] * yc[1] + m.chi2 * cth * cth;
   double thdot = yc[5] / Sig;                                   // Eq. (60)
   double lamc = lam + sig * h;
-  bool trusted = fabs(thdot) >= ip.thdot_min &&
+  // events count only inside the integration domain R_cap <= R <= R_esc
+  bool trusted = yc[1] >= ip.R_cap && yc[1] <= ip.R_esc && fabs(thdot) >= ip.thdot_min &&
                  (!cs.have_trusted || lamc - cs.lam_last >= ip.dlam_min);
   if (!trusted) return;
   int n = cs.ncross;
@@ -260,10 +291,30 @@ __device__ __forceinline__ bool reflect_axis(double& th, double& pth, double& ph
   return true;
 }
 
+__device__ __forceinline__ CrossOut cross_out(const TraceArgs& a, int64_t item, uint32_t img) {
+  CrossOut co;
+  co.R_em = co.phi_em = co.T_em = co.g = nullptr;
+  co.stride = a.npix;
+  co.pix = -1;
+  co.rec = nullptr;
+  if (a.mode == 1) {
+    co.rec = &a.rec[item];
+  } else if (a.level == 0) {
+    const OutPtrs& o = a.out[img];
+    co.R_em = o.R_em;
+    co.phi_em = o.phi_em;
+    co.T_em = o.T_em;
+    co.g = o.g;
+    co.pix = item - (int64_t)img * a.npix;
+  }
+  return co;
+}
+
 // One attempted FP64 step.  Returns 0 while the ray continues, else the
 // terminal status + 1 (1 escaped, 2 captured, 3 undetermined).
 __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConsts<double>& m,
-                                          Ray64& r, const CrossOut& co) {
+                                          Ray64& r, const TraceArgs& a, int64_t item,
+                                          uint32_t img) {
   const double h = r.h;
   double k[7][6];
 #pragma unroll
@@ -319,7 +370,15 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
         hf0[i] = h * k[0][i];
         hf1[i] = h * k[6][i];
       }
-      handle_crossing(ip, m, r.E, r.ell, r.y, y1, hf0, hf1, hd, r.lam, h, r.cs, co);
+      // copies: the ray state must not have its address taken (it would be
+      // demoted from registers to local memory for every step)
+      double y0c[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) y0c[i] = r.y[i];
+      CrossState cs = r.cs;
+      const CrossOut co = cross_out(a, item, img);
+      handle_crossing(ip, m, r.E, r.ell, y0c, y1, hf0, hf1, hd, r.lam, h, cs, co);
+      r.cs = cs;
     }
   }
   r.lam += h;
@@ -421,25 +480,6 @@ __device__ __forceinline__ void resolve_item(const TraceArgs& a, int64_t idx, ui
     pix = -1;
   }
   cell_centre(a.ip[img], key, X, Y);
-}
-
-__device__ __forceinline__ CrossOut cross_out(const TraceArgs& a, int64_t item, uint32_t img) {
-  CrossOut co;
-  co.R_em = co.phi_em = co.T_em = co.g = nullptr;
-  co.stride = a.npix;
-  co.pix = -1;
-  co.rec = nullptr;
-  if (a.mode == 1) {
-    co.rec = &a.rec[item];
-  } else if (a.level == 0) {
-    const OutPtrs& o = a.out[img];
-    co.R_em = o.R_em;
-    co.phi_em = o.phi_em;
-    co.T_em = o.T_em;
-    co.g = o.g;
-    co.pix = item - (int64_t)img * a.npix;
-  }
-  return co;
 }
 
 // Terminal write of a ray: the per-ray record of its level (for refinement

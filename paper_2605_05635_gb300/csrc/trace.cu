@@ -67,9 +67,8 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
       continue;
     }
     if (active) {
-      const CrossOut co = cross_out(a, item, img);
       const int acc0 = r.nacc, rej0 = r.nrej;
-      int term = ray_step64(*ip, m, r, co);
+      int term = ray_step64(*ip, m, r, a, item, img);
       w_acc += (unsigned long long)(r.nacc - acc0);
       w_rej += (unsigned long long)(r.nrej - rej0);
       if (term) {

@@ -125,6 +125,155 @@ struct MxConsts {
   float rtol, atol, R_cap, R_esc, promote_R, demote_R;
 };
 
+// Launch of the mixed path: the constants of motion and the launch momenta
+// in FP64 (Eqs. 70-74, as in ray_init64), the state as float pairs, and the
+// Hairer-Wanner starting step in FP32.
+__device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricConsts<float>& mf,
+                                            const MxConsts& c, double X, double Y, RayMx& r) {
+  const double d = sqrt(ip.r_obs * ip.r_obs + X * X + Y * Y), id = 1.0 / d;
+  r.ell = ip.sq_gph * (-X * id);
+  r.E = ip.zamo_N + ip.zamo_w * r.ell;
+  df_from(0.0, r.yh[0], r.yl[0]);
+  df_from(ip.r_obs, r.yh[1], r.yl[1]);
+  df_from(ip.incl, r.yh[2], r.yl[2]);
+  df_from(0.0, r.yh[3], r.yl[3]);
+  df_from(ip.sq_grr * (-ip.r_obs * id), r.yh[4], r.yl[4]);
+  df_from(ip.sq_gth * (-Y * id), r.yh[5], r.yl[5]);
+  r.Ef = (float)r.E;
+  r.ellf = (float)r.ell;
+  float W, P2;
+  geo_rhs(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f, W, P2);
+  float d0 = 0.f, d1 = 0.f, sc[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    sc[i] = c.atol + c.rtol * fabsf(r.yh[i]);
+    d0 += (r.yh[i] / sc[i]) * (r.yh[i] / sc[i]);
+    d1 += (r.f[i] / sc[i]) * (r.f[i] / sc[i]);
+  }
+  d0 = sqrtf(d0 / 6.f);
+  d1 = sqrtf(d1 / 6.f);
+  const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * d0 / d1;
+  float f1[6];
+  geo_rhs(mf, r.Ef, r.ellf, r.yh[1] + h0 * r.f[1], r.yh[2] + h0 * r.f[2], r.yh[4] + h0 * r.f[4],
+          r.yh[5] + h0 * r.f[5], f1, W, P2);
+  float d2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float q = (f1[i] - r.f[i]) / sc[i];
+    d2 += q * q;
+  }
+  d2 = sqrtf(d2 / 6.f) / h0;
+  const float mx = fmaxf(d1, d2);
+  const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : exp2f(0.2f * log2f(0.01f / mx));
+  r.h = fminf(100.f * h0, h1);
+  r.lh = r.ll = 0.f;
+  r.cs.lam_last = 0.0;
+  r.cs.have_trusted = false;
+  r.cs.ncross = 0;
+  r.cs.I[0] = r.cs.I[1] = r.cs.I[2] = r.cs.I[3] = 0.0;
+  r.rejected = false;
+  r.nacc = r.nrej = r.steps = 0;
+  r.hdrift = 0.f;
+}
+
+// Redshift of a prograde circular emitter (Eqs. 89-91), FP32.
+__device__ __forceinline__ bool emitter_g_f(const MetricConsts<float>& m, float R, float E,
+                                            float ell, float& g) {
+  float H, dH;
+  lapse(m, R, 1.f / R, H, dH);
+  const float den = 2.f * R - m.chi2 * dH, disc = 2.f * R * dH;
+  if (!(disc >= 0.f) || den == 0.f) return false;
+  const float W = (-m.chi * dH + sqrtf(disc)) / den;
+  const float gtt = -H, gtp = -m.chi * (1.f - H), gpp = R * R + m.chi2 + m.chi2 * (1.f - H);
+  const float norm = -(gtt + 2.f * W * gtp + W * W * gpp);
+  if (!(norm > 0.f)) return false;
+  g = sqrtf(norm) / (E - W * ell);
+  return true;
+}
+
+// Crossing inside an accepted FP32 step: the rule of handle_crossing with an
+// FP32 root of theta - pi/2 on the dense output and FP32 transfer maps,
+// redshift and emissivity (Eqs. 82-91); the affine parameter of the trusted
+// gap test and the intensity sums stay in FP64.
+static __device__ __noinline__ void cross_f32(const ImgParams& ip, const MetricConsts<float>& m,
+                                             float Ef, float ellf, const float* y0h,
+                                             const float* y0l, const float* y1h,
+                                             const float* y1l, const float* hf0,
+                                             const float* hf1, const float* hd, double lam,
+                                             float h, CrossState& cs, const CrossOut& co) {
+  constexpr float kHPh = 1.57079637050628662109375f, kHPl = -4.37113900018624283e-8f;
+  // dense output of one component relative to an offset (hi, lo) pair
+  auto dense = [&](int i, float sig, float off_h, float off_l) {
+    const float y0 = __fadd_rn(__fsub_rn(y0h[i], off_h), __fsub_rn(y0l[i], off_l));
+    const float r2 = __fadd_rn(__fsub_rn(y1h[i], y0h[i]), __fsub_rn(y1l[i], y0l[i]));
+    const float r3 = hf0[i] - r2, r4 = r2 - hf1[i] - r3;
+    return y0 + sig * (r2 + (1.f - sig) * (r3 + sig * (r4 + (1.f - sig) * hd[i])));
+  };
+  const float s0 = dense(2, 0.f, kHPh, kHPl), s1 = dense(2, 1.f, kHPh, kHPl);
+  float sig = 1.f;
+  if (s1 != 0.f) {
+    float x0 = 0.f, f0 = s0, x1 = 1.f, f1 = s1;
+    for (int it = 0; it < 60; ++it) {
+      float x2 = x1 - f1 * (x1 - x0) / (f1 - f0);
+      if (!(x2 > fminf(x0, x1) && x2 < fmaxf(x0, x1))) x2 = 0.5f * (x0 + x1);
+      const float f2 = dense(2, x2, kHPh, kHPl);
+      if (f2 == 0.f) {
+        x1 = x2;
+        break;
+      }
+      if ((f2 > 0.f) != (f1 > 0.f)) {
+        x0 = x1;
+        f0 = f1;
+      } else {
+        f0 *= 0.5f;
+      }
+      x1 = x2;
+      f1 = f2;
+      if (fabsf(x1 - x0) <= 1e-7f || fabsf(f2) <= 1e-8f) break;
+    }
+    sig = x1;
+  }
+  const float Rc = dense(1, sig, 0.f, 0.f);
+  const float pth = dense(5, sig, 0.f, 0.f);
+  const float thdot = pth / (Rc * Rc);  // Eq. (60) on the plane (cos theta = 0)
+  const double lamc = lam + (double)(sig * h);
+  if (!(Rc >= (float)ip.R_cap && Rc <= (float)ip.R_esc && fabsf(thdot) >= (float)ip.thdot_min &&
+        (!cs.have_trusted || lamc - cs.lam_last >= ip.dlam_min)))
+    return;
+  const int n = cs.ncross;
+  float g = 0.f, j = 0.f;
+  if (emitter_g_f(m, Rc, Ef, ellf, g)) {
+    const float Rin = (float)ip.R_in;
+    const float tin = 0.5f * (1.f + tanhf((Rc - Rin) / (float)ip.sig_in));
+    const float tout = 0.5f * (1.f - tanhf((Rc - (float)ip.R_out) / (float)ip.sig_out));
+    j = (float)ip.j0 * exp2f(-(float)ip.p * log2f(Rc / Rin)) * __expf(-(Rc - Rin) / (float)ip.R_s) *
+        tin * tout;
+  }
+  const float In = g * g * g * j;
+  cs.I[0] += (double)In;
+  if (n < 3) {
+    cs.I[1 + n] = (double)In;
+    float ph = fmodf(dense(3, sig, 0.f, 0.f), 6.28318530717958647692f);
+    if (ph < 0.f) ph += 6.28318530717958647692f;
+    if (co.pix >= 0) {
+      const int64_t o = n * co.stride + co.pix;
+      if (co.R_em) co.R_em[o] = Rc;
+      if (co.phi_em) co.phi_em[o] = ph;
+      if (co.T_em) co.T_em[o] = dense(0, sig, 0.f, 0.f);
+      if (co.g) co.g[o] = g;
+    }
+    if (co.rec) {
+      co.rec->R_em[n] = Rc;
+      co.rec->phi_em[n] = ph;
+      co.rec->T_em[n] = dense(0, sig, 0.f, 0.f);
+      co.rec->g[n] = g;
+    }
+  }
+  cs.ncross = n + 1;
+  cs.lam_last = lamc;
+  cs.have_trusted = true;
+}
+
 // pi/2 as a float pair hi + lo, and pi (hi part) for the axis test.
 constexpr float kHalfPiHi = 1.57079637050628662109375f;
 constexpr float kHalfPiLo = -4.37113900018624283e-8f;
@@ -134,7 +283,8 @@ constexpr float kPiHi = 3.1415927410125732421875f;
 // when the ray must be promoted to FP64.
 __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricConsts<float>& mf,
                                            const MetricConsts<double>& md, const MxConsts& c,
-                                           RayMx& r, const CrossOut& co, bool may_promote) {
+                                           RayMx& r, const TraceArgs& a, int64_t item,
+                                           uint32_t img, bool may_promote) {
   const float h = r.h;
   float k[7][6];
 #pragma unroll
@@ -148,7 +298,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     for (int i = 0; i < 6; ++i) {
       float acc = 0.f;
 #pragma unroll
-      for (int j = 0; j < s; ++j) acc += (float)kDP.a[s][j] * k[j][i];
+      for (int j = 0; j < s; ++j) acc += kDPf.a[s][j] * k[j][i];
       ys[i] = r.yh[i] + (r.yl[i] + h * acc);
     }
     bool ok = geo_rhs(mf, r.Ef, r.ellf, ys[1], ys[2], ys[4], ys[5], k[s], W, P2oD);
@@ -160,8 +310,8 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     float a5 = 0.f, ae = 0.f;
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
-      a5 += (float)kDP.b[j] * k[j][i];
-      ae += (float)kDP.e[j] * k[j][i];
+      a5 += kDPf.b[j] * k[j][i];
+      ae += kDPf.e[j] * k[j][i];
     }
     dlt[i] = h * a5;
     float sc = c.atol + c.rtol * fmaxf(fabsf(r.yh[i]), fabsf(r.yh[i] + dlt[i]));
@@ -189,20 +339,23 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     float s0 = __fadd_rn(__fsub_rn(r.yh[2], kHalfPiHi), __fsub_rn(r.yl[2], kHalfPiLo));
     float s1 = __fadd_rn(__fsub_rn(nh[2], kHalfPiHi), __fsub_rn(nl[2], kHalfPiLo));
     if ((s0 > 0.f && s1 <= 0.f) || (s0 < 0.f && s1 >= 0.f)) {
-      double y0[6], y1[6], hf0[6], hf1[6], hd[6];
+      float y0h[6], y0l[6], hf0[6], hf1[6], hd[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        float a = 0.f;
+        float acc = 0.f;
 #pragma unroll
-        for (int j = 0; j < 7; ++j) a += (float)kDP.d[j] * k[j][i];
-        y0[i] = df_to(r.yh[i], r.yl[i]);
-        y1[i] = df_to(nh[i], nl[i]);
-        hd[i] = (double)h * (double)a;
-        hf0[i] = (double)h * (double)k[0][i];
-        hf1[i] = (double)h * (double)k[6][i];
+        for (int j = 0; j < 7; ++j) acc += kDPf.d[j] * k[j][i];
+        y0h[i] = r.yh[i];
+        y0l[i] = r.yl[i];
+        hd[i] = h * acc;
+        hf0[i] = h * k[0][i];
+        hf1[i] = h * k[6][i];
       }
-      handle_crossing(ip, md, r.E, r.ell, y0, y1, hf0, hf1, hd, df_to(r.lh, r.ll), (double)h,
-                      r.cs, co);
+      CrossState cs = r.cs;  // copies keep the ray state in registers
+      const CrossOut co = cross_out(a, item, img);
+      cross_f32(ip, mf, r.Ef, r.ellf, y0h, y0l, nh, nl, hf0, hf1, hd, df_to(r.lh, r.ll), h, cs,
+                co);
+      r.cs = cs;
     }
   }
   df_add(r.lh, r.ll, h);
@@ -276,9 +429,9 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
           ip = &a.ip[img];
           mf = metric_consts<float>(*ip);
           md = metric_consts<double>(*ip);
-          Ray64 r64;
-          ray_init64(*ip, md, X, Y, r64);
-          mx_from64(r64, r);
+          c.rtol = (float)fmax(ip->rtol, 1e-9);  // FP32 noise floor of the estimate
+          c.atol = (float)ip->atol;
+          ray_init_mx(*ip, mf, c, X, Y, r);
         }
         c.rtol = (float)fmax(ip->rtol, 1e-9);  // FP32 noise floor of the estimate
         c.atol = (float)ip->atol;
@@ -296,9 +449,8 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
       continue;
     }
     if (active) {
-      const CrossOut co = cross_out(a, item, img);
       const int acc0 = r.nacc, rej0 = r.nrej;
-      int term = ray_step_mx(*ip, mf, md, c, r, co, may_promote);
+      int term = ray_step_mx(*ip, mf, md, c, r, a, item, img, may_promote);
       w_acc += (unsigned long long)(r.nacc - acc0);
       w_rej += (unsigned long long)(r.nrej - rej0);
       if (term == 4) {

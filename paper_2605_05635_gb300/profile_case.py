@@ -32,7 +32,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     plan.check()
     st = plan.stats()
-    print(f"case {a.case} {a.precision}: rays {sum(st['rays'])} accepted {st['accepted_steps']}")
+    print(f"case {a.case} {a.precision}: rays {sum(st['rays'])} accepted fp32 "
+          f"{st['accepted_fp32']} fp64 {st['accepted_fp64']} promoted {st['promoted_rays']}")
     plan.close()
 
 

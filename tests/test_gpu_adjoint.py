@@ -1,0 +1,128 @@
+"""Gradients from the hand-written discrete adjoint (bh_trace_backward)
+against central finite differences of the FP64 oracle with the same adaptive
+decisions frozen (each ray replays its nominal accepted step sequence; the
+refinement pattern is the nominal one).
+
+Loss: L = sum_p w_p I_p + sum_m c_m D_m with random weights w, c and
+D = (centroid offset C, asymmetry A_LR, bright-ring radius rho_peak
+(parabolic vertex), |V|/|V(0,0)| at 8 seeded baselines).  Bar: each
+component within 1e-4 relative of the finite difference (plus a floor of
+1e-6 of the largest component for components that vanish).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from parity import oracle_flat
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["chi", "incl", "halo1", "halo2", "j0", "p", "R_s", "sigma_in", "sigma_out", "R_out"]
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_05635_gb300 as B
+    B.lib()
+    return B
+
+
+def _cells(flat, keys):
+    """Screen points and leaf weights of every traced cell of the nominal
+    image (base pixels and refined cells), in the oracle's arithmetic."""
+    nx, ny = flat["nx"], flat["ny"]
+    dx = (flat["x_max"] - flat["x_min"]) / nx
+    dy = (flat["y_max"] - flat["y_min"]) / ny
+
+    def split(k):
+        lev = (k >> 12) & 0xF
+        digits = tuple((k >> (4 * (3 - l))) & 0xF for l in range(1, lev + 1))
+        return k >> 16, lev, digits
+
+    cells = [split(int(k)) for k in keys]
+    parents = {(b, lev - 1, d[:-1]) for b, lev, d in cells}
+    pts, w, pix = [], [], []
+    for q in range(nx * ny):
+        i, j = q % nx, q // nx
+        pts.append((flat["x_min"] + (i + 0.5) * dx, flat["y_min"] + (j + 0.5) * dy))
+        w.append(0.0 if (q, 0, ()) in parents else 1.0)
+        pix.append(q)
+    for b, lev, d in cells:
+        i, j = b % nx, b // nx
+        X = flat["x_min"] + (i + 0.5) * dx
+        Y = flat["y_min"] + (j + 0.5) * dy
+        wx, wy = dx, dy
+        for dig in d:
+            X = X + ((dig % 4 + 0.5) / 4.0 - 0.5) * wx
+            Y = Y + ((dig // 4 + 0.5) / 4.0 - 0.5) * wy
+            wx, wy = wx / 4.0, wy / 4.0
+        pts.append((X, Y))
+        w.append(0.0 if (b, lev, d) in parents else 16.0 ** (-lev))
+        pix.append(b)
+    return np.array(pts), np.array(w), np.array(pix)
+
+
+def _loss(oracle, flat, I, wI, cdiag, uv8):
+    from oracle.diagnostics import diagnostics, rho_peak_smooth
+    from oracle.visibility import visibilities
+    ext = (flat["x_min"], flat["x_max"], flat["y_min"], flat["y_max"])
+    d = diagnostics(I, *ext)
+    rho = rho_peak_smooth(I, *ext)
+    V = visibilities(I, *ext, np.concatenate([[[0.0, 0.0]], uv8]))
+    amp = np.abs(V[1:]) / abs(V[0])
+    D = np.concatenate([[d["C"], d["A_LR"], rho], amp])
+    return float(np.sum(wI * I) + np.sum(cdiag * D)), D
+
+
+def _frozen_image(oracle, flat, pts, w, pix, hbuf, counts):
+    P = oracle.problem(**oracle_flat(flat, oracle))
+    r = oracle.trace_points_frozen(P, pts, hbuf, counts)
+    I = np.zeros(flat["nx"] * flat["ny"])
+    np.add.at(I, pix, w * r["I_tot"])
+    return I.reshape(flat["ny"], flat["nx"])
+
+
+@pytest.mark.parametrize("metric", [0, 2, 1])
+def test_adjoint_matches_frozen_finite_differences(B, oracle, metric):
+    import torch
+    from paper_2605_05635_gb300 import workloads
+    flat = dict(workloads.kerr_64(), metric=metric, chi=0.7, incl=math.radians(50.0), nx=14,
+                ny=12, x_min=-12.0, x_max=12.0, y_min=-10.0, y_max=10.0, levels=1, r_in_mode=1,
+                **workloads.HALO[metric])
+    rng = np.random.default_rng(20260514 + metric)
+    wI = rng.normal(size=(flat["ny"], flat["nx"]))
+    cdiag = rng.normal(size=11) * np.array([1, 1, 1] + [5] * 8)
+    uv8 = workloads.uv_points(8, seed=20260514)
+    st, cam, em, it = B.from_flat(flat)
+    grad, diag, img = B.trace_backward(st, cam, em, it, dL_dI=torch.from_numpy(wI).float(),
+                                       dL_ddiag=cdiag, uv8=uv8)
+    keys_gpu = B.trace_image(st, cam, em, it, keys_cap=1 << 16)["refine_keys"].cpu().numpy()
+    P0 = oracle.problem(**oracle_flat(flat, oracle))
+    nominal = oracle.trace_image(P0)
+    assert np.array_equal(np.sort(keys_gpu.astype(np.uint64)), nominal["keys"])
+    pts, w, pix = _cells(flat, nominal["keys"])
+    rec, hbuf, counts = oracle.trace_points_record(P0, pts, hcap=8000)
+    I0 = _frozen_image(oracle, flat, pts, w, pix, hbuf, counts)
+    assert np.allclose(I0, nominal["I"], rtol=1e-12, atol=1e-15)
+    _, D0 = _loss(oracle, flat, I0, wI, cdiag, uv8)
+    assert np.allclose(diag, D0, rtol=1e-5, atol=1e-9)
+    keys = {0: "chi", 1: "incl", 2: {1: "lam_E", 2: "eta"}.get(metric), 3: "lam_c" if metric == 2 else None,
+            4: "j0", 5: "p", 6: "R_s", 7: "sigma_in", 8: "sigma_out", 9: "R_out"}
+    fd = np.zeros(10)
+    for k, name in keys.items():
+        if name is None:
+            continue
+        x0 = flat[name]
+        h = 1e-6 if name in ("chi", "incl") else 1e-6 * abs(x0)
+        lp, _ = _loss(oracle, flat, _frozen_image(oracle, dict(flat, **{name: x0 + h}), pts, w, pix,
+                                                  hbuf, counts), wI, cdiag, uv8)
+        lm, _ = _loss(oracle, flat, _frozen_image(oracle, dict(flat, **{name: x0 - h}), pts, w, pix,
+                                                  hbuf, counts), wI, cdiag, uv8)
+        fd[k] = (lp - lm) / (2 * h)
+    floor = 1e-6 * np.max(np.abs(fd))
+    for k in range(10):
+        assert abs(grad[k] - fd[k]) <= 1e-4 * abs(fd[k]) + floor, (NAMES[k], grad[k], fd[k])
