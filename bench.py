@@ -228,6 +228,7 @@ def main():
         steps_acc = 0
         trace_ms = 0.0
         steps64, ms64, promoted = 0, 0.0, 0
+        max_steps_ray = 0
         launches = 0
         for _ in range(args.steps):
             plan.launch(stream=stream)
@@ -243,6 +244,7 @@ def main():
                 ms64 += st["fp64_ms"]
                 promoted += st["promoted_rays"]
             launches += st["kernel_launches"]
+            max_steps_ray = max(max_steps_ray, st["max_ray_steps"])
             if st["status"] != 0:
                 raise SystemExit(f"device status {st['status']}")
         t1.record(stream)
@@ -320,11 +322,19 @@ def main():
         # image's maximum, over pixels whose class and refinement depth agree
         # (a pixel whose class or subtree differs holds a ray whose class is
         # not determined at FP32 precision: counted, not measured)
-        errs, p999, excluded, total = [], [], 0, 0
-        for a, b in zip(plan.outputs, rp.outputs):
+        errs, p999, excluded, total, worst = [], [], 0, 0, None
+        for img, (a, b) in enumerate(zip(plan.outputs, rp.outputs)):
             same = ((a["status"] == b["status"]) & (a["ncross"] == b["ncross"]) &
                     (a["refine_level"] == b["refine_level"]))
             d = (a["I"].double() - b["I"].double()).abs() / b["I"].double().abs().max()
+            dm = torch.where(same, d, torch.zeros_like(d))
+            k = int(torch.argmax(dm))
+            jj, ii = divmod(k, dm.shape[1])
+            if worst is None or float(dm.flatten()[k]) > worst["err"]:
+                worst = {"err": float(dm.flatten()[k]), "image": img, "i": ii, "j": jj,
+                         "I_mixed": float(a["I"][jj, ii]), "I_fp64": float(b["I"][jj, ii]),
+                         "ncross": int(b["ncross"][jj, ii]), "status": int(b["status"][jj, ii]),
+                         "level": int(b["refine_level"][jj, ii])}
             errs.append(float(d[same].max()))
             p999.append(float(torch.quantile(d.flatten()[::7], 0.999)))
             excluded += int((~same).sum())
@@ -333,7 +343,8 @@ def main():
                    "mixed_over_fp64": value / (sum(st["rays"]) / (c1 - c0)),
                    "max_rel_intensity_err_vs_fp64": max(errs),
                    "p99_9_rel_intensity_err_all_pixels": max(p999),
-                   "pixels_with_class_or_depth_change": excluded, "pixels": total}
+                   "pixels_with_class_or_depth_change": excluded, "pixels": total,
+                   "worst_pixel": worst}
         rp.close()
 
     if rank == 0:
@@ -351,7 +362,7 @@ def main():
             "images_per_s": images_per_s,
             "rays_per_step": all_rays / args.steps / world,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
-            "gpu_launches": launches, "compare": compare,
+            "gpu_launches": launches, "compare": compare, "longest_ray_steps": max_steps_ray,
         }
         print(json.dumps(line), flush=True)
     plan.close()

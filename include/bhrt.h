@@ -208,6 +208,7 @@ typedef struct {
   int64_t rejected_fp32;   /* mixed precision: rejected FP32 trial steps      */
   int64_t promoted_rays;   /* mixed precision: rays handed to the FP64 pass   */
   int64_t spill_full;      /* promotions refused because the queue was full   */
+  int64_t max_ray_steps;   /* attempted steps of the longest ray              */
   double trace_ms[4];      /* per-level trace time (all passes) of the last
                               launch when timing is on, else -1               */
   double fp32_ms, fp64_ms; /* trace kernel time by precision (timing on)      */

@@ -82,6 +82,7 @@ class RunStats(C.Structure):
                 ("accepted_fp64", C.c_int64), ("rejected_fp64", C.c_int64),
                 ("accepted_fp32", C.c_int64), ("rejected_fp32", C.c_int64),
                 ("promoted_rays", C.c_int64), ("spill_full", C.c_int64),
+                ("max_ray_steps", C.c_int64),
                 ("trace_ms", C.c_double * 4), ("fp32_ms", C.c_double), ("fp64_ms", C.c_double),
                 ("kernel_launches", C.c_int32), ("status", C.c_int32),
                 ("trace_blocks", C.c_int32), ("trace_threads", C.c_int32)]

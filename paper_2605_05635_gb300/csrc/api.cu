@@ -761,6 +761,7 @@ bh_status bh_plan_stats(bh_plan p, void* stream, bh_run_stats* out) {
   out->rejected_fp32 = (int64_t)h.rejected32;
   out->promoted_rays = (int64_t)h.promoted_rays;
   out->spill_full = (int64_t)h.spill_full;
+  out->max_ray_steps = (int64_t)h.max_ray_steps;
   out->kernel_launches = p->launches;
   out->status = h.status;
   out->trace_blocks = p->shape.blocks;

@@ -51,6 +51,7 @@ struct alignas(256) WsHeader {
   unsigned long long qcount[2][kMaxLevels + 1];  // queue lengths
   unsigned long long promoted_rays;          // rays handed to FP64
   unsigned long long spill_full;             // promotions refused (queue full)
+  unsigned long long max_ray_steps;          // longest ray (attempted steps)
 };
 
 // Structure-of-arrays records of one refinement level.

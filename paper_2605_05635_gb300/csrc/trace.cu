@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
   uint32_t img = 0;
   bool active = false, drained = false;
   unsigned iter = 0;
+  unsigned long long w_max = 0;
   unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_full = 0;
 
   while (true) {
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
       if (term) {
         finish_ray(a, item, img, term - 1, r.cs, r.hdrift, r.nacc, r.nrej, r.E, r.ell, r.lam);
         w_rays += 1ull;
+        w_max = (unsigned long long)r.steps > w_max ? (unsigned long long)r.steps : w_max;
         active = false;
       } else if (a.allow_spill && r.nacc != acc0 && r.y[1] > ip->demote_R && r.y[4] > 0.0) {
         // outgoing beyond the strong-field zone: finish in FP32
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
   flush_tally(&a.hdr->accepted, w_acc, lane);
   flush_tally(&a.hdr->rejected, w_rej, lane);
   flush_tally(&a.hdr->rays[a.level], w_rays, lane);
+  if (w_max) atomicMax(&a.hdr->max_ray_steps, w_max);
   flush_tally(&a.hdr->spill_full, w_full, lane);
 }
 

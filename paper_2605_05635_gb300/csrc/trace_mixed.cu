@@ -12,7 +12,8 @@
 //   - launch, constants of motion (E, ell), starting step, crossing roots,
 //     transfer maps, redshift and emissivity run in FP64;
 //   - a ray is promoted to the FP64 kernel when it comes within promote_R of
-//     the horizon or, winding at N_cross >= 2, is inside demote_R; the FP64
+//     the horizon or, winding to image order n >= 2 (N_cross >= 3, Sec. 4.2),
+//     is inside demote_R; the FP64
 //     pass hands it back once it is outgoing beyond demote_R, and a second
 //     FP32 pass (no further promotion) finishes it.  Promotion is a hand-off
 //     through a queue rather than a per-lane branch, so warps never mix FP64
@@ -386,7 +387,8 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   if (R > c.R_esc) return 1;
   r.h = h * step_factor(err, r.rejected);
   r.rejected = false;
-  if (may_promote && (R < c.promote_R || (r.cs.ncross >= 2 && R < c.demote_R))) return 4;
+  // image order n = N_cross - 1 (Sec. 4.2): rays winding to n >= 2 are promoted
+  if (may_promote && (R < c.promote_R || (r.cs.ncross >= 3 && R < c.demote_R))) return 4;
   return r.steps >= ip.max_steps ? 3 : 0;
 }
 
@@ -406,6 +408,7 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
   uint32_t img = 0;
   bool active = false, drained = false;
   unsigned iter = 0;
+  unsigned long long w_max = 0;
   unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_promo = 0, w_full = 0;
 
   while (true) {
@@ -466,6 +469,7 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
         finish_ray(a, item, img, term - 1, r.cs, r.hdrift, r.nacc, r.nrej, r.E, r.ell,
                    df_to(r.lh, r.ll));
         w_rays += 1ull;
+        w_max = (unsigned long long)r.steps > w_max ? (unsigned long long)r.steps : w_max;
         active = false;
       }
     }
@@ -480,6 +484,7 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
   flush_tally(&a.hdr->accepted32, w_acc, lane);
   flush_tally(&a.hdr->rejected32, w_rej, lane);
   flush_tally(&a.hdr->rays[a.level], w_rays, lane);
+  if (w_max) atomicMax(&a.hdr->max_ray_steps, w_max);
   flush_tally(&a.hdr->promoted_rays, w_promo, lane);
   flush_tally(&a.hdr->spill_full, w_full, lane);
 }
