@@ -116,6 +116,11 @@ typedef struct {
   double dlambda_min;   /* and an affine gap >= this to the previous one    */
   double promote_dr;    /* mixed: FP64 steps while R < R_+ + promote_dr     */
   double time_budget_s; /* device time budget per call (s); 0 = none      */
+  int32_t promote_order;/* mixed: rays reaching image order n >= this
+                           (n = N_cross - 1, Sec. 4.2) inside R = 10 take
+                           FP64 steps until outgoing beyond R = 10;
+                           0..1000, 1000 = never                          */
+  int32_t reserved;     /* must be 0                                        */
 } bh_integrator;
 
 /* Per-pixel output planes (device pointers, caller-owned).  Any pointer
@@ -215,6 +220,12 @@ typedef struct {
   int32_t kernel_launches; /* kernels enqueued per launch                     */
   int32_t status;          /* device status word (bh_status)                  */
   int32_t trace_blocks, trace_threads; /* trace launch shape in use           */
+  /* Persistent-queue timeline per trace pass (0 main, 1 FP64 promoted,
+   * 2 FP32 demoted) and level, from the device clock: bulk = first warp
+   * start to the first warp finding the queue empty; tail = from then to
+   * the last warp exit (warps running with idle lanes).  -1 if not run. */
+  double bulk_ms[3][4];
+  double tail_ms[3][4];
 } bh_run_stats;
 
 /* Validates, computes per-image constants and uploads them to the
@@ -241,6 +252,8 @@ typedef struct {
   int32_t blocks[2];       /* chosen grid: [0] main trace kernel, [1] FP64 pass */
   int32_t threads[2];      /* chosen block size                               */
   double best_ms[2];       /* trace time of the whole launch with the choice  */
+  int32_t variant[2];      /* kernel build chosen: 0 registers unbounded,
+                              1 capped for 4 blocks of 128 per SM (mixed only) */
 } bh_tune_report;
 bh_status bh_plan_autotune(bh_plan plan, void* stream, bh_tune_report* report);
 

@@ -58,7 +58,8 @@ class _Integrator(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_steps", C.c_int32), ("rtol", C.c_double),
                 ("atol", C.c_double), ("cap_factor", C.c_double), ("esc_factor", C.c_double),
                 ("thetadot_min", C.c_double), ("dlambda_min", C.c_double),
-                ("promote_dr", C.c_double), ("time_budget_s", C.c_double)]
+                ("promote_dr", C.c_double), ("time_budget_s", C.c_double),
+                ("promote_order", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _ImageOut(C.Structure):
@@ -85,18 +86,22 @@ class RunStats(C.Structure):
                 ("max_ray_steps", C.c_int64),
                 ("trace_ms", C.c_double * 4), ("fp32_ms", C.c_double), ("fp64_ms", C.c_double),
                 ("kernel_launches", C.c_int32), ("status", C.c_int32),
-                ("trace_blocks", C.c_int32), ("trace_threads", C.c_int32)]
+                ("trace_blocks", C.c_int32), ("trace_threads", C.c_int32),
+                ("bulk_ms", (C.c_double * 4) * 3), ("tail_ms", (C.c_double * 4) * 3)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         for k in ("cells", "rays", "trace_ms"):
             d[k] = list(d[k])
+        for k in ("bulk_ms", "tail_ms"):
+            d[k] = [list(r) for r in d[k]]
         return d
 
 
 class TuneReport(C.Structure):
     _fields_ = [("candidates", C.c_int32), ("blocks", C.c_int32 * 2),
-                ("threads", C.c_int32 * 2), ("best_ms", C.c_double * 2)]
+                ("threads", C.c_int32 * 2), ("best_ms", C.c_double * 2),
+                ("variant", C.c_int32 * 2)]
 
 
 # ----------------------------------------------------------- user parameters
@@ -160,11 +165,13 @@ class Integrator:
     dlambda_min: float = 1e-6
     promote_dr: float = 0.1
     time_budget_s: float = 0.0
+    promote_order: int = 2
 
     def _c(self):
         return _Integrator(self.precision, self.max_steps, self.rtol, self.atol,
                            self.cap_factor, self.esc_factor, self.thetadot_min,
-                           self.dlambda_min, self.promote_dr, self.time_budget_s)
+                           self.dlambda_min, self.promote_dr, self.time_budget_s,
+                           self.promote_order, 0)
 
 
 def from_flat(d: dict):
@@ -187,7 +194,8 @@ def from_flat(d: dict):
                     thetadot_min=d.get("thetadot_min", 1e-8),
                     dlambda_min=d.get("dlambda_min", 1e-6),
                     promote_dr=d.get("promote_dr", 0.1),
-                    time_budget_s=d.get("time_budget_s", 0.0))
+                    time_budget_s=d.get("time_budget_s", 0.0),
+                    promote_order=d.get("promote_order", 2))
     return st, cam, em, it
 
 
@@ -418,7 +426,8 @@ class Plan:
         _check(lib().bh_plan_autotune(self._h, _stream_ptr(stream), C.byref(rep)),
                "bh_plan_autotune")
         return dict(candidates=rep.candidates, blocks=list(rep.blocks),
-                    threads=list(rep.threads), best_ms=list(rep.best_ms))
+                    threads=list(rep.threads), best_ms=list(rep.best_ms),
+                    variant=list(rep.variant))
 
     def set_timing(self, enable: bool):
         _check(lib().bh_plan_set_timing(self._h, int(enable)), "bh_plan_set_timing")

@@ -185,7 +185,8 @@ bh_status validate(const bh_spacetime& s, const bh_camera& c, const bh_emission&
   if (g.precision < 0 || g.precision > kMaxPrecision || g.max_steps < 1) return BH_ERR_INVALID_ARG;
   if (!finite_pos(g.rtol) || !finite_pos(g.atol) || !(g.cap_factor >= 1.0) ||
       !(g.esc_factor > 1.0) || !(g.thetadot_min >= 0.0) || !(g.dlambda_min >= 0.0) ||
-      !(g.promote_dr >= 0.0) || !(g.time_budget_s >= 0.0))
+      !(g.promote_dr >= 0.0) || !(g.time_budget_s >= 0.0) || g.promote_order < 0 ||
+      g.promote_order > 1000 || g.reserved != 0)
     return BH_ERR_INVALID_ARG;
   return BH_OK;
 }
@@ -252,6 +253,7 @@ bh_status make_params(const bh_spacetime& s, const bh_camera& c, const bh_emissi
   ip.dlam_min = g.dlambda_min;
   ip.promote_R = rp + g.promote_dr;
   ip.demote_R = kDemoteR;
+  ip.promote_ncross = g.promote_order + 1;
   return BH_OK;
 }
 
@@ -766,6 +768,14 @@ bh_status bh_plan_stats(bh_plan p, void* stream, bh_run_stats* out) {
   out->status = h.status;
   out->trace_blocks = p->shape.blocks;
   out->trace_threads = p->shape.threads;
+  for (int pass = 0; pass < 3; ++pass)
+    for (int l = 0; l <= kMaxLevels; ++l) {
+      const unsigned long long b = h.t_pass[0][pass][l], d = h.t_pass[1][pass][l],
+                               e = h.t_pass[2][pass][l];
+      const bool ok = b && d && e && d >= b && e >= d;
+      out->bulk_ms[pass][l] = ok ? (double)(d - b) * 1e-6 : -1.0;
+      out->tail_ms[pass][l] = ok ? (double)(e - d) * 1e-6 : -1.0;
+    }
   return BH_OK;
 }
 
@@ -799,11 +809,15 @@ bh_status bh_plan_autotune(bh_plan p, void* stream, bh_tune_report* rep) {
   for (int which = 0; which < (p->precision == 1 ? 2 : 1); ++which) {
     LaunchShape& sh = which == 0 ? p->shape : p->shape64;
     const int prec = which == 0 ? p->precision : 0;
-    const int occ = trace_default_blocks_per_sm(prec, 128);
-    LaunchShape cand[16];
+    LaunchShape cand[24];
     int nc = 0;
-    for (int b = 1; b <= occ && nc < 12; ++b) cand[nc++] = LaunchShape{sms * b, 128};
-    cand[nc++] = LaunchShape{sms * 2 * occ, 64};
+    const int nvar = prec == 1 ? kMixedVariants : 1;
+    for (int v = 0; v < nvar; ++v) {
+      const int occ = trace_default_blocks_per_sm(prec, 128, v);
+      for (int b = (v == 0 ? 1 : occ); b <= occ && nc < 20; ++b)
+        cand[nc++] = LaunchShape{sms * b, 128, v};
+      cand[nc++] = LaunchShape{sms * 2 * occ, 64, v};
+    }
     LaunchShape best = sh;
     double best_ms = 1e300;
     for (int c = 0; c < nc; ++c) {
@@ -822,6 +836,7 @@ bh_status bh_plan_autotune(bh_plan p, void* stream, bh_tune_report* rep) {
       rep->best_ms[which] = best_ms;
       rep->blocks[which] = best.blocks;
       rep->threads[which] = best.threads;
+      rep->variant[which] = best.variant;
     }
   }
   if (rep) rep->candidates = tried;

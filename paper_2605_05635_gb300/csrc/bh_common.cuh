@@ -32,6 +32,8 @@ struct alignas(16) ImgParams {
   double r_plus, R_cap, R_esc, R_in;
   double j0, p, R_s, sig_in, sig_out, R_out;
   double rtol, atol, thdot_min, dlam_min, promote_R, demote_R;
+  int32_t promote_ncross;  // mixed: promote once N_cross reaches this inside demote_R
+  int32_t pad1;
 };
 
 // Workspace header (first 256 bytes of every workspace).
@@ -52,6 +54,11 @@ struct alignas(256) WsHeader {
   unsigned long long promoted_rays;          // rays handed to FP64
   unsigned long long spill_full;             // promotions refused (queue full)
   unsigned long long max_ray_steps;          // longest ray (attempted steps)
+  // Timeline of each trace pass (0 main, 1 FP64 promoted, 2 FP32 demoted)
+  // per level, %globaltimer ns: [0] first warp start, [1] first warp to
+  // find the queue empty, [2] last warp exit.  The span [1]..[2] is the
+  // tail in which warps run with idle lanes.
+  unsigned long long t_pass[3][3][kMaxLevels + 1];
 };
 
 // Structure-of-arrays records of one refinement level.

@@ -560,6 +560,12 @@ __device__ __forceinline__ int64_t claim(unsigned long long* head, bool need, in
   return need ? (int64_t)base + __popc(mask & ((1u << lane) - 1u)) : -1;
 }
 
+// Pass timeline marks (WsHeader::t_pass): the first writer of a slot wins.
+__device__ __forceinline__ void mark_first(unsigned long long* slot) {
+  if (*reinterpret_cast<volatile unsigned long long*>(slot) == 0ull)
+    atomicCAS(slot, 0ull, globaltimer());
+}
+
 // Warp sum of lane tallies, one atomic per warp.
 __device__ __forceinline__ void flush_tally(unsigned long long* dst, unsigned long long v,
                                             int lane) {

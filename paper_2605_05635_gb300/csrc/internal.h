@@ -58,12 +58,14 @@ struct TraceArgs {
 struct LaunchShape {
   int blocks;
   int threads;
+  int variant = 0;  // mixed kernel: 0 register-unbounded build, 1 built for 4 blocks/SM
 };
 
 // trace.cu / trace_mixed.cu
 cudaError_t launch_trace_fp64(const TraceArgs& a, LaunchShape s, cudaStream_t st);
 cudaError_t launch_trace_mixed(const TraceArgs& a, LaunchShape s, cudaStream_t st);
-int trace_default_blocks_per_sm(int precision, int threads);
+int trace_default_blocks_per_sm(int precision, int threads, int variant = 0);
+constexpr int kMixedVariants = 2;
 size_t spill_record_bytes();
 const void* trace_fp64_kernel_ptr();
 

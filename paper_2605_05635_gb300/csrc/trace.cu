@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
   unsigned long long w_max = 0;
   unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_full = 0;
 
+  const int pass = a.source;
+  if (lane == 0) mark_first(&a.hdr->t_pass[0][pass][a.level]);
   while (true) {
     const bool need = !active && !drained;
     int64_t idx = claim(a.head, need, lane);
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
         active = true;
       } else {
         drained = true;
+        mark_first(&a.hdr->t_pass[1][pass][a.level]);
       }
     }
     if (__ballot_sync(kFull, active) == 0) {
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
   flush_tally(&a.hdr->accepted, w_acc, lane);
   flush_tally(&a.hdr->rejected, w_rej, lane);
   flush_tally(&a.hdr->rays[a.level], w_rays, lane);
+  if (lane == 0) atomicMax(&a.hdr->t_pass[2][pass][a.level], globaltimer());
   if (w_max) atomicMax(&a.hdr->max_ray_steps, w_max);
   flush_tally(&a.hdr->spill_full, w_full, lane);
 }

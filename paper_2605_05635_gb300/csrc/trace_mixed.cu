@@ -124,6 +124,7 @@ __device__ __forceinline__ void mx_resume(const SpillRec& s, const MetricConsts<
 
 struct MxConsts {
   float rtol, atol, R_cap, R_esc, promote_R, demote_R;
+  int promote_nc;
 };
 
 // Launch of the mixed path: the constants of motion and the launch momenta
@@ -387,12 +388,18 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   if (R > c.R_esc) return 1;
   r.h = h * step_factor(err, r.rejected);
   r.rejected = false;
-  // image order n = N_cross - 1 (Sec. 4.2): rays winding to n >= 2 are promoted
-  if (may_promote && (R < c.promote_R || (r.cs.ncross >= 3 && R < c.demote_R))) return 4;
+  // image order n = N_cross - 1 (Sec. 4.2): rays winding to n >= promote_order
+  // are promoted
+  if (may_promote && (R < c.promote_R || (r.cs.ncross >= c.promote_nc && R < c.demote_R)))
+    return 4;
   return r.steps >= ip.max_steps ? 3 : 0;
 }
 
-__global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
+// MinBlocks = 0 leaves the register count to the compiler (3 blocks of 128
+// threads per SM); MinBlocks = 4 caps it at 128 registers for 4 blocks at a
+// small spill cost.  The autotuner picks between them.
+template <int MinBlocks>
+__global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t n_items = pass_items(a);
   const unsigned long long budget = a.hdr->budget_ns;
@@ -411,6 +418,8 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
   unsigned long long w_max = 0;
   unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_promo = 0, w_full = 0;
 
+  const int pass = (a.source ? 2 : 0);
+  if (lane == 0) mark_first(&a.hdr->t_pass[0][pass][a.level]);
   while (true) {
     const bool need = !active && !drained;
     int64_t idx = claim(a.head, need, lane);
@@ -442,9 +451,11 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
         c.R_esc = (float)ip->R_esc;
         c.promote_R = (float)ip->promote_R;
         c.demote_R = (float)ip->demote_R;
+        c.promote_nc = ip->promote_ncross;
         active = true;
       } else {
         drained = true;
+        mark_first(&a.hdr->t_pass[1][pass][a.level]);
       }
     }
     if (__ballot_sync(kFull, active) == 0) {
@@ -484,22 +495,28 @@ __global__ void __launch_bounds__(128) trace_mixed_kernel(TraceArgs a) {
   flush_tally(&a.hdr->accepted32, w_acc, lane);
   flush_tally(&a.hdr->rejected32, w_rej, lane);
   flush_tally(&a.hdr->rays[a.level], w_rays, lane);
+  if (lane == 0) atomicMax(&a.hdr->t_pass[2][pass][a.level], globaltimer());
   if (w_max) atomicMax(&a.hdr->max_ray_steps, w_max);
   flush_tally(&a.hdr->promoted_rays, w_promo, lane);
   flush_tally(&a.hdr->spill_full, w_full, lane);
 }
 
 cudaError_t launch_trace_mixed(const TraceArgs& a, LaunchShape s, cudaStream_t st) {
-  trace_mixed_kernel<<<s.blocks, s.threads, 0, st>>>(a);
+  if (s.variant == 1)
+    trace_mixed_kernel<4><<<s.blocks, s.threads, 0, st>>>(a);
+  else
+    trace_mixed_kernel<0><<<s.blocks, s.threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-int trace_default_blocks_per_sm(int precision, int threads) {
+int trace_default_blocks_per_sm(int precision, int threads, int variant) {
   int nb = 0;
   if (precision == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_fp64_kernel_ptr(), threads, 0);
+  else if (variant == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel<4>, threads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel<0>, threads, 0);
   return nb > 0 ? nb : 1;
 }
 

@@ -74,10 +74,11 @@ def test_argument_errors_return_before_device_work(B):
     code = lib.bh_trace_points(C.byref(st), C.byref(far), C.byref(em), C.byref(it), 0, None,
                                None, ws, 0, None)
     assert code == 3
-    badint = B.Integrator(precision=7)._c()
-    code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(em), C.byref(badint), 0,
-                               None, None, ws, 0, None)
-    assert code == 1
+    for badint in (B.Integrator(precision=7)._c(), B.Integrator(promote_order=-1)._c(),
+                   B.Integrator(promote_order=1001)._c()):
+        code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(em), C.byref(badint), 0,
+                                   None, None, ws, 0, None)
+        assert code == 1
     incl = B.Camera(incl=math.pi)._c()
     code = lib.bh_trace_points(C.byref(st), C.byref(incl), C.byref(em), C.byref(it), 0, None,
                                None, ws, 0, None)
