@@ -38,6 +38,7 @@ WORKLOAD = ("512x512 sweep: {Einasto lam_E=0.1, cored-NFW eta=0.02 lam_c=10, Ker
 # counted; the Einasto / cored-NFW lapses add work that is not counted either.
 FLOP_PER_STEP = 6 * 84 + 504
 FP64_PEAK_FLOPS = 1.25e12          # GB300 nominal FP64 vector rate
+KEYS_CAP = 1 << 23                 # refinement-pattern keys kept per image
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
@@ -129,9 +130,286 @@ def cpu_baseline(flats, seconds: float, seed: int = 7):
             pixels += len(ij)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": rays / elapsed, "unit": "rays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{pixels} random base pixels (16 per image per round, 6 images) with "
+            "sample": f"{pixels} random base pixels (16 per image per round, {len(flats)} images) with "
                       f"their on-screen neighbours and refinement subtrees, {rays} rays, "
                       f"{elapsed:.1f} s of oracle time"}
+
+
+METRIC_SWEEP96 = "images/s, 96-image sweep at 256^2 (batched, graph-captured) vs single-image FP64"
+WORKLOAD_SWEEP96 = ("96 images: {Kerr, Einasto lam_E=0.1, cored-NFW eta=0.02 lam_c=10} x a in "
+                    "{0,0.3,0.5,0.7,0.8,0.9,0.94,0.98} x incl {17,30,50,80} deg, halo x U(0.8,1.2) "
+                    "(seed 20260513), 256^2 over +-12 M, 4x4 refinement x3 levels")
+METRIC_VIS = "visibilities/s, 1024^2 image x 65536 baselines (Eq. 108), split BF16 tensor cores"
+WORKLOAD_VIS = ("1024^2 cored-NFW a=0.94 incl 17 deg +-12 M refined image; 65536 (u,v) with "
+                "|b| ~ U(0,15) G-lambda, PA ~ U(0,pi), theta_g = 3.8 uas (seed 20260515)")
+
+
+def _events_ms(stream, fn, reps):
+    import torch
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(reps):
+        fn()
+    t1.record(stream)
+    t1.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def _compare_images(a, b):
+    """Intensity error of a against b relative to b's maximum over pixels
+    whose class and refinement depth agree."""
+    import torch
+    same = ((a["status"] == b["status"]) & (a["ncross"] == b["ncross"]) &
+            (a["refine_level"] == b["refine_level"]))
+    d = (a["I"].double() - b["I"].double()).abs() / b["I"].double().abs().max()
+    return (float(d[same].max()), float(torch.quantile(d.flatten()[::7], 0.999)),
+            int((~same).sum()))
+
+
+def _subtree_changed(a, b, nx, ny):
+    """Pixels whose set of refined cells differs between two outputs."""
+    import numpy as np
+    ka = a["refine_keys"][: int(a["refine_keys_count"][0])].cpu().numpy()
+    kb = b["refine_keys"][: int(b["refine_keys_count"][0])].cpu().numpy()
+    diff = np.setxor1d(ka, kb)
+    mask = np.zeros(nx * ny, dtype=bool)
+    mask[np.unique(diff >> 16)] = True
+    return mask.reshape(ny, nx)
+
+
+def compare_with_fp64(B, workloads, flats, plan, dev, stream, value):
+    """The same images by the all-FP64 path at its own tolerance (rtol 1e-10):
+    its throughput, and the mixed images' intensity error relative to each
+    image's maximum.  Pixels whose class or refinement depth differs are
+    counted, not measured; pixels whose refined subtree differs (a refined
+    cell changed class, which near the critical curve a perturbation of
+    1e-7 already does) are measured separately."""
+    import torch
+    ref_items = [B.from_flat(dict(d, **workloads.FP64_INTEG)) for d in flats]
+    rp = B.Plan(ref_items, device=dev, keys_cap=KEYS_CAP)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize(dev)
+        c0 = time.perf_counter()
+        rp.launch(stream=stream)
+        st = rp.stats(stream)
+        c1 = time.perf_counter()
+    errs, errs_tree, p999, p9999, over, excluded, tree_changed, total = [], [], [], [], 0, 0, 0, 0
+    worst = None
+    for img, (a, b) in enumerate(zip(plan.outputs, rp.outputs)):
+        same = ((a["status"] == b["status"]) & (a["ncross"] == b["ncross"]) &
+                (a["refine_level"] == b["refine_level"]))
+        tree = same & ~torch.from_numpy(_subtree_changed(a, b, flats[img]["nx"],
+                                                         flats[img]["ny"])).to(same.device)
+        d = (a["I"].double() - b["I"].double()).abs() / b["I"].double().abs().max()
+        dm = torch.where(same, d, torch.zeros_like(d))
+        k = int(torch.argmax(dm))
+        jj, ii = divmod(k, dm.shape[1])
+        if worst is None or float(dm.flatten()[k]) > worst["err"]:
+            worst = {"err": float(dm.flatten()[k]), "image": img, "i": ii, "j": jj,
+                     "I_mixed": float(a["I"][jj, ii]), "I_fp64": float(b["I"][jj, ii]),
+                     "ncross": int(b["ncross"][jj, ii]), "status": int(b["status"][jj, ii]),
+                     "level": int(b["refine_level"][jj, ii]),
+                     "subtree_changed": bool(not tree[jj, ii])}
+        errs.append(float(d[same].max()))
+        errs_tree.append(float(d[tree].max()))
+        over += int((dm > 1e-4).sum())
+        flat = d.flatten()
+        p999.append(float(torch.quantile(flat[::3], 0.999)))
+        p9999.append(float(torch.quantile(flat[::3], 0.9999)))
+        excluded += int((~same).sum())
+        tree_changed += int((same & ~tree).sum())
+        total += same.numel()
+    fp64_rate = sum(st["rays"]) / (c1 - c0)
+    rp.close()
+    return {"fp64_rtol": workloads.FP64_INTEG["rtol"], "fp64_rays_per_s": fp64_rate,
+            "fp64_s_per_step": c1 - c0, "mixed_over_fp64": value / fp64_rate,
+            "max_rel_intensity_err_vs_fp64": max(errs),
+            "max_rel_intensity_err_same_subtree": max(errs_tree),
+            "pixels_over_1e-4": over,
+            "p99_9_rel_intensity_err_all_pixels": max(p999),
+            "p99_99_rel_intensity_err_all_pixels": max(p9999),
+            "pixels_with_class_or_depth_change": excluded,
+            "pixels_with_refined_subtree_change": tree_changed, "pixels": total,
+            "worst_pixel": worst}
+
+
+def run_sweep96(args, B, workloads, dev, stream):
+    """The 96-image sweep in one batched plan, autotuned and replayed as a
+    CUDA graph; single-image FP64 tracing of a sample of the images is the
+    comparison."""
+    import torch
+    prec = B.MIXED if args.precision == "mixed" else B.FP64
+    base = workloads.sweep_96()
+    flats = [dict(d, **(workloads.MIXED_INTEG if prec == B.MIXED else workloads.FP64_INTEG))
+             for d in base]
+    items = [B.from_flat(d) for d in flats]
+    plan = B.Plan(items, device=dev)
+    with torch.cuda.stream(stream):
+        plan.launch(stream=stream)
+        plan.check(stream)
+        tune = plan.autotune(stream=stream) if args.autotune else None
+        # one timed eager launch for the per-kernel split (roofline)
+        plan.set_timing(True)
+        plan.launch(stream=stream)
+        st = plan.stats(stream)
+        plan.set_timing(False)
+        for _ in range(args.warmup):
+            plan.launch(use_graph=True, stream=stream)
+        plan.check(stream)
+        sampler = ClockSampler(dev.index or 0)
+        torch.cuda.synchronize(dev)
+        sampler.start()
+        ms = _events_ms(stream, lambda: plan.launch(use_graph=True, stream=stream), args.steps)
+        clocks = sampler.stop()
+        plan.check(stream)
+        rays = sum(plan.stats(stream)["rays"])
+    images_per_s = len(items) / (ms / 1e3)
+    steps32, ms32 = st["accepted_fp32"], st["fp32_ms"]
+    steps64, ms64 = st["accepted_fp64"], st["fp64_ms"]
+    if prec == B.FP64:
+        flops, kms, peak, kern = steps64 * FLOP_PER_STEP, ms64, FP64_PEAK_FLOPS, "trace_fp64_kernel"
+    else:
+        flops, kms, peak, kern = steps32 * FLOP_PER_STEP, ms32, FP32_PEAK_FLOPS, "trace_mixed_kernel"
+    achieved = flops / (kms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved * 1e12 / peak, "traffic": None, "kernel": kern,
+                "kernel_share_of_step": kms / (st["fp32_ms"] + st["fp64_ms"]) if kms > 0 else None,
+                "lane_util": st["lane_util_fp32" if prec == B.MIXED else "lane_util_fp64"]}
+    # single-image FP64 tracing of a sample (one image per spin, all metrics)
+    sample = list(range(0, len(base), 12))
+    t_single, errs, p999, changed = [], [], [], 0
+    for k in sample:
+        it = B.from_flat(dict(base[k], **workloads.FP64_INTEG))
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize(dev)
+            c0 = time.perf_counter()
+            ref = B.trace_batch([it], device=dev, stream=stream)[0]
+            torch.cuda.synchronize(dev)
+            t_single.append(time.perf_counter() - c0)
+        e, p, c = _compare_images(plan.outputs[k], ref)
+        errs.append(e)
+        p999.append(p)
+        changed += c
+    fp64_images_per_s = len(sample) / sum(t_single)
+    line = {
+        "metric": METRIC_SWEEP96, "value": images_per_s, "unit": "images/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == B.FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SWEEP96, "images": len(items), "nx": 256, "ny": 256,
+                   "levels": 3, "precision": args.precision, "graph": True,
+                   "autotuned": tune is not None,
+                   "l2": "working set > L2 (refinement records ~GBs); no flush",
+                   "parallelism": "dp1"},
+        "rays_per_s": rays / (ms / 1e3), "rays_per_step": rays, "tune": tune,
+        "roofline": roofline, "clocks": clocks, "gpu_launches": st["kernel_launches"],
+        "compare": {"fp64_single_image_images_per_s": fp64_images_per_s,
+                    "batched_over_fp64_single": images_per_s / fp64_images_per_s,
+                    "sampled_images": sample,
+                    "max_rel_intensity_err_vs_fp64": max(errs),
+                    "p99_9_rel_intensity_err": max(p999),
+                    "pixels_with_class_or_depth_change": changed},
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def run_vis1024(args, B, workloads, dev, stream):
+    """Eq. (108) for 65,536 baselines of a traced 1024^2 image on the tensor
+    cores (split BF16 and FP16), against the FP64 direct sum on a sample."""
+    import numpy as np
+    import torch
+    flat = workloads.vis_1024()
+    item = B.from_flat(flat)
+    cam = item[1]
+    with torch.cuda.stream(stream):
+        I = B.trace_batch([item], device=dev, stream=stream)[0]["I"]
+    K = 65536
+    uv_np = workloads.uv_points(K, seed=20260515)
+    uv = torch.from_numpy(uv_np).to(dev)
+    imax = float(I.abs().max())
+    vout = torch.empty(K, 2, dtype=torch.float64, device=dev)
+    res = {}
+    with torch.cuda.stream(stream):
+        for mode, name in ((B.VIS_BF16, "bf16"), (B.VIS_FP16, "fp16")):
+            def call():
+                B.visibilities(I, cam, uv, mode=mode, image_max=imax, stream=stream, out=vout,
+                               check=False)
+            for _ in range(args.warmup):
+                call()
+            torch.cuda.synchronize(dev)
+            sampler = ClockSampler(dev.index or 0)
+            sampler.start()
+            ms = _events_ms(stream, call, args.steps)
+            clocks = sampler.stop()
+            V = torch.view_as_complex(vout.clone())
+            res[name] = {"ms": ms, "clocks": clocks, "V": V}
+        ks = torch.arange(0, K, 16, device=dev)
+        ref = B.visibilities_fp64(I, cam, uv[ks], stream=stream)
+        torch.cuda.synchronize(dev)
+        V0 = abs(complex(B.visibilities_fp64(I, cam, torch.zeros(1, 2, dtype=torch.float64,
+                                                                  device=dev))[0]))
+    n = flat["nx"]
+    tc_flop = 3 * 4.0 * n * n * K        # three split products of the two real GEMMs
+    alg_flop = 4.0 * n * n * K
+    ms = res["bf16"]["ms"]
+    errs = {k: float((v["V"][ks] - ref).abs().max() / V0) for k, v in res.items()}
+    achieved = tc_flop / (ms / 1e3) / 1e12
+    peak = _measured_peak("bf16_tflops") or 1900.0
+    # end to end: host image in, visibilities out, through the public call
+    I_host = I.cpu().pin_memory()
+    V_host = torch.empty(K, 2, dtype=torch.float64, pin_memory=True)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            Id = I_host.to(dev, non_blocking=True)
+            B.visibilities(Id, cam, uv, mode=B.VIS_BF16, image_max=imax, stream=stream,
+                           out=vout, check=False)
+            V_host.copy_(vout, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        w1 = time.perf_counter()
+    e2e = {"value": K * args.steps / (w1 - w0), "unit": "visibilities/s",
+           "h2d_bytes_per_step": I_host.numel() * 4, "d2h_bytes_per_step": K * 16}
+    # oracle: the direct per-baseline sum on the host for a bounded sample
+    from oracle.visibility import visibilities as vis_oracle
+    Ih = I.double().cpu().numpy()
+    c0 = time.perf_counter()
+    kk = 0
+    while time.perf_counter() - c0 < args.cpu_seconds and kk < K:
+        vis_oracle(Ih, flat["x_min"], flat["x_max"], flat["y_min"], flat["y_max"], uv_np[kk:kk + 8])
+        kk += 8
+    cpu_s = time.perf_counter() - c0
+    line = {
+        "metric": METRIC_VIS, "value": K / (ms / 1e3), "unit": "visibilities/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 split -> f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_VIS, "nx": n, "ny": n, "baselines": K,
+                   "l2": "image 4 MB, phases generated on chip; inputs stay resident",
+                   "parallelism": "dp1"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "vis_tc_kernel",
+                     "tensor_flop_per_launch": tc_flop, "algorithmic_flop": alg_flop,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+        "fp16_split": {"ms": res["fp16"]["ms"], "max_err_vs_fp64_over_V0": errs["fp16"]},
+        "max_err_vs_fp64_over_V0": errs["bf16"], "fp64_sample": int(ks.numel()),
+        "clocks": res["bf16"]["clocks"], "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "cpu_baseline": {"value": kk / cpu_s, "unit": "visibilities/s", "cores": 1,
+                         "kind": "oracle", "sample": f"{kk} baselines of the same image, numpy "
+                         f"direct sum (Eq. 108), {cpu_s:.1f} s"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _measured_peak(key):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        v = d.get(key)
+        return float(v) if v is not None else None
+    except (OSError, ValueError, TypeError):
+        return None
 
 
 def run_reference(args, rank, world):
@@ -170,6 +448,10 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--workload", choices=["sweep512", "sweep96", "vis1024"], default="sweep512",
+                    help="sweep512: the headline line; sweep96 and vis1024: the batched-sweep "
+                         "and visibility measurements")
+    ap.add_argument("--autotune", action="store_true", help="sweep96: autotune the plan first")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -204,13 +486,19 @@ def main():
         bhrt.Integrator(precision=prec)
         flats = workloads.sweep_512(precision=prec)
         items = [B.from_flat(d) for d in flats]
-        plan = B.Plan(items, device=dev)
+        plan = B.Plan(items, device=dev, keys_cap=KEYS_CAP)
     except B.BHRTError:
         prec = B.FP64
         flats = workloads.sweep_512(precision=prec)
         items = [B.from_flat(d) for d in flats]
-        plan = B.Plan(items, device=dev)
+        plan = B.Plan(items, device=dev, keys_cap=KEYS_CAP)
     stream = torch.cuda.Stream(device=dev)
+    if args.workload != "sweep512":
+        if world > 1:
+            raise SystemExit("--workload sweep96/vis1024 run on one GPU")
+        plan.close()
+        fn = run_sweep96 if args.workload == "sweep96" else run_vis1024
+        return fn(args, B, workloads, dev, stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -285,9 +573,11 @@ def main():
     e2e = None
     with torch.cuda.stream(stream):
         outs = plan.outputs
+        # the image planes come back to the host (the refinement-key buffers stay)
+        planes = [{k: v for k, v in o.items() if k != "refine_keys"} for o in outs]
         host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()}
-                for o in outs]
-        d2h = sum(v.numel() * v.element_size() for o in outs for v in o.values())
+                for o in planes]
+        d2h = sum(v.numel() * v.element_size() for o in planes for v in o.values())
         h2d = len(items) * 512  # per-image constants + output pointers uploaded per call
         ws = plan.workspace
         n_e2e = max(1, min(3, args.steps))
@@ -299,8 +589,8 @@ def main():
             res = B.trace_batch(items, device=dev, stream=stream, outputs=outs, workspace=ws,
                                 check=False)
             for o, h in zip(res, host):
-                for k, v in o.items():
-                    h[k].copy_(v, non_blocking=True)
+                for k in h:
+                    h[k].copy_(o[k], non_blocking=True)
             torch.cuda.synchronize(dev)
             e_rays += rays / args.steps
         w1 = time.perf_counter()
@@ -310,42 +600,7 @@ def main():
 
     compare = None
     if prec == B.MIXED and not args.no_compare:
-        ref_items = [B.from_flat(dict(d, precision=B.FP64)) for d in flats]
-        rp = B.Plan(ref_items, device=dev)
-        with torch.cuda.stream(stream):
-            torch.cuda.synchronize(dev)
-            c0 = time.perf_counter()
-            rp.launch(stream=stream)
-            st = rp.stats(stream)
-            c1 = time.perf_counter()
-        # error of the mixed images against the FP64 images, relative to each
-        # image's maximum, over pixels whose class and refinement depth agree
-        # (a pixel whose class or subtree differs holds a ray whose class is
-        # not determined at FP32 precision: counted, not measured)
-        errs, p999, excluded, total, worst = [], [], 0, 0, None
-        for img, (a, b) in enumerate(zip(plan.outputs, rp.outputs)):
-            same = ((a["status"] == b["status"]) & (a["ncross"] == b["ncross"]) &
-                    (a["refine_level"] == b["refine_level"]))
-            d = (a["I"].double() - b["I"].double()).abs() / b["I"].double().abs().max()
-            dm = torch.where(same, d, torch.zeros_like(d))
-            k = int(torch.argmax(dm))
-            jj, ii = divmod(k, dm.shape[1])
-            if worst is None or float(dm.flatten()[k]) > worst["err"]:
-                worst = {"err": float(dm.flatten()[k]), "image": img, "i": ii, "j": jj,
-                         "I_mixed": float(a["I"][jj, ii]), "I_fp64": float(b["I"][jj, ii]),
-                         "ncross": int(b["ncross"][jj, ii]), "status": int(b["status"][jj, ii]),
-                         "level": int(b["refine_level"][jj, ii])}
-            errs.append(float(d[same].max()))
-            p999.append(float(torch.quantile(d.flatten()[::7], 0.999)))
-            excluded += int((~same).sum())
-            total += same.numel()
-        compare = {"fp64_rays_per_s": sum(st["rays"]) / (c1 - c0),
-                   "mixed_over_fp64": value / (sum(st["rays"]) / (c1 - c0)),
-                   "max_rel_intensity_err_vs_fp64": max(errs),
-                   "p99_9_rel_intensity_err_all_pixels": max(p999),
-                   "pixels_with_class_or_depth_change": excluded, "pixels": total,
-                   "worst_pixel": worst}
-        rp.close()
+        compare = compare_with_fp64(B, workloads, flats, plan, dev, stream, value)
 
     if rank == 0:
         cpu = cpu_baseline(flats, args.cpu_seconds) if world == 1 else None

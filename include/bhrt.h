@@ -226,6 +226,9 @@ typedef struct {
    * the last warp exit (warps running with idle lanes).  -1 if not run. */
   double bulk_ms[3][4];
   double tail_ms[3][4];
+  /* Mean fraction of the 32 lanes holding a ray over the stepping-loop
+   * iterations of the FP32 and FP64 trace kernels (-1 if not run). */
+  double lane_util_fp32, lane_util_fp64;
 } bh_run_stats;
 
 /* Validates, computes per-image constants and uploads them to the
@@ -253,7 +256,7 @@ typedef struct {
   int32_t threads[2];      /* chosen block size                               */
   double best_ms[2];       /* trace time of the whole launch with the choice  */
   int32_t variant[2];      /* kernel build chosen: 0 registers unbounded,
-                              1 capped for 4 blocks of 128 per SM (mixed only) */
+                              1 capped (FP64: 3 blocks of 128 per SM; mixed: 4) */
 } bh_tune_report;
 bh_status bh_plan_autotune(bh_plan plan, void* stream, bh_tune_report* report);
 

@@ -87,7 +87,8 @@ class RunStats(C.Structure):
                 ("trace_ms", C.c_double * 4), ("fp32_ms", C.c_double), ("fp64_ms", C.c_double),
                 ("kernel_launches", C.c_int32), ("status", C.c_int32),
                 ("trace_blocks", C.c_int32), ("trace_threads", C.c_int32),
-                ("bulk_ms", (C.c_double * 4) * 3), ("tail_ms", (C.c_double * 4) * 3)]
+                ("bulk_ms", (C.c_double * 4) * 3), ("tail_ms", (C.c_double * 4) * 3),
+                ("lane_util_fp32", C.c_double), ("lane_util_fp64", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -121,7 +121,8 @@ __device__ int adj_step(const ImgParams& ip, const MetricConsts<double>& m, Ray6
     }
     bad |= !geo_rhs(m, r.E, r.ell, ys[1], ys[2], ys[4], ys[5], k[s], W, P2);
   }
-  double y1[6], err2 = 0.0;
+  double y1[6];
+  float err2 = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     double a5 = 0.0, ae = 0.0;
@@ -131,11 +132,9 @@ __device__ int adj_step(const ImgParams& ip, const MetricConsts<double>& m, Ray6
       ae += kDP.e[j] * k[j][i];
     }
     y1[i] = r.y[i] + h * a5;
-    double sc = ip.atol + ip.rtol * fmax(fabs(r.y[i]), fabs(y1[i]));
-    double q = h * ae / sc;
-    err2 += q * q;
+    err2 += err_term(r.y[i], y1[i], h * ae, ip.atol, ip.rtol);
   }
-  float err = (float)sqrt(err2 / 6.0);
+  float err = sqrtf(err2 / 6.f);
   r.steps++;
   if (bad || !(err <= 1.f)) {
     r.h = bad ? 0.5 * h : h * (double)step_factor(err, true);

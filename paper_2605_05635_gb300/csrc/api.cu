@@ -776,6 +776,8 @@ bh_status bh_plan_stats(bh_plan p, void* stream, bh_run_stats* out) {
       out->bulk_ms[pass][l] = ok ? (double)(d - b) * 1e-6 : -1.0;
       out->tail_ms[pass][l] = ok ? (double)(e - d) * 1e-6 : -1.0;
     }
+  out->lane_util_fp32 = h.warp_iters[0] ? (double)h.lane_iters[0] / (32.0 * h.warp_iters[0]) : -1.0;
+  out->lane_util_fp64 = h.warp_iters[1] ? (double)h.lane_iters[1] / (32.0 * h.warp_iters[1]) : -1.0;
   return BH_OK;
 }
 
@@ -811,7 +813,7 @@ bh_status bh_plan_autotune(bh_plan p, void* stream, bh_tune_report* rep) {
     const int prec = which == 0 ? p->precision : 0;
     LaunchShape cand[24];
     int nc = 0;
-    const int nvar = prec == 1 ? kMixedVariants : 1;
+    const int nvar = kKernelVariants;
     for (int v = 0; v < nvar; ++v) {
       const int occ = trace_default_blocks_per_sm(prec, 128, v);
       for (int b = (v == 0 ? 1 : occ); b <= occ && nc < 20; ++b)

@@ -59,6 +59,10 @@ struct alignas(256) WsHeader {
   // find the queue empty, [2] last warp exit.  The span [1]..[2] is the
   // tail in which warps run with idle lanes.
   unsigned long long t_pass[3][3][kMaxLevels + 1];
+  // Stepping-loop iterations of the trace kernels ([0] FP32, [1] FP64) and
+  // the lanes with a ray in them: lane utilisation of the persistent loop.
+  unsigned long long warp_iters[2];
+  unsigned long long lane_iters[2];
 };
 
 // Structure-of-arrays records of one refinement level.
@@ -127,16 +131,18 @@ __device__ __forceinline__ bool geo_rhs(const MetricConsts<T>& m, T E, T ell, T 
                                         T pth, T d[6], T& W, T& P2oD) {
   T s, c;
   d_sincos(th, &s, &c);
-  T iR = d_rcp(R);
+  T R2 = R * R;
+  T Sig = R2 + m.chi2 * c * c;               // Eq. (23)
+  // the lapse needs 1/R before Delta exists: 1/R and 1/Sigma from one
+  // reciprocal of R Sigma, then 1/Delta and 1/sin(theta) from one more
+  T iRS = d_rcp(R * Sig);
+  T iR = Sig * iRS, iS = R * iRS;
   T H, dH;
   lapse(m, R, iR, H, dH);
-  T R2 = R * R;
   T Dl = R2 * H + m.chi2;                    // Eq. (25)
   T dDl = T(2) * R * H + R2 * dH;            // Eq. (35)
-  T Sig = R2 + m.chi2 * c * c;               // Eq. (23)
-  T iS = d_rcp(Sig);
-  T iD = d_rcp(Dl);
-  T is = d_rcp(s);
+  T iDs = d_rcp(Dl * s);
+  T iD = s * iDs, is = Dl * iDs;
   T r2a2 = R2 + m.chi2;
   T P = r2a2 * E - m.chi * ell;
   T Q = ell * is - m.chi * E * s;

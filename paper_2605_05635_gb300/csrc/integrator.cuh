@@ -312,6 +312,16 @@ __device__ __forceinline__ CrossOut cross_out(const TraceArgs& a, int64_t item, 
 
 // One attempted FP64 step.  Returns 0 while the ray continues, else the
 // terminal status + 1 (1 escaped, 2 captured, 3 undetermined).
+// One component's squared scaled error (h e_i / sc_i)^2 with the scale
+// sc_i = atol + rtol max(|y0_i|, |y1_i|) in FP64 and the ratio in FP32: the
+// norm only decides acceptance and the next step factor, to a few digits.
+__device__ __forceinline__ float err_term(double y0, double y1, double he, double atol,
+                                          double rtol) {
+  const double sc = atol + rtol * fmax(fabs(y0), fabs(y1));
+  const float q = __fdividef((float)he, (float)sc);
+  return q * q;
+}
+
 __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConsts<double>& m,
                                           Ray64& r, const TraceArgs& a, int64_t item,
                                           uint32_t img) {
@@ -334,7 +344,8 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     bool ok = geo_rhs(m, r.E, r.ell, ys[1], ys[2], ys[4], ys[5], k[s], W, P2oD);
     bad |= !ok;
   }
-  double y1[6], err2 = 0.0;
+  double y1[6];
+  float err2 = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     double a5 = 0.0, ae = 0.0;
@@ -344,11 +355,9 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
       ae += kDP.e[j] * k[j][i];
     }
     y1[i] = r.y[i] + h * a5;
-    double sc = ip.atol + ip.rtol * fmax(fabs(r.y[i]), fabs(y1[i]));
-    double q = h * ae / sc;
-    err2 += q * q;
+    err2 += err_term(r.y[i], y1[i], h * ae, ip.atol, ip.rtol);
   }
-  float err = (float)sqrt(err2 / 6.0);
+  float err = sqrtf(err2 / 6.f);
   r.steps++;
   if (bad || !(err <= 1.f)) {
     r.h = bad ? 0.5 * h : h * (double)step_factor(err, true);

@@ -58,16 +58,17 @@ struct TraceArgs {
 struct LaunchShape {
   int blocks;
   int threads;
-  int variant = 0;  // mixed kernel: 0 register-unbounded build, 1 built for 4 blocks/SM
+  int variant = 0;  // 0 register-unbounded build; 1 capped build (FP64: 3 blocks of
+                    // 128 per SM, mixed: 4)
 };
 
 // trace.cu / trace_mixed.cu
 cudaError_t launch_trace_fp64(const TraceArgs& a, LaunchShape s, cudaStream_t st);
 cudaError_t launch_trace_mixed(const TraceArgs& a, LaunchShape s, cudaStream_t st);
 int trace_default_blocks_per_sm(int precision, int threads, int variant = 0);
-constexpr int kMixedVariants = 2;
+constexpr int kKernelVariants = 2;
 size_t spill_record_bytes();
-const void* trace_fp64_kernel_ptr();
+const void* trace_fp64_kernel_ptr(int variant);
 
 // refine.cu
 struct RefineArgs {

@@ -21,7 +21,11 @@
 
 namespace bhrt {
 
-__global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
+// MinBlocks = 0 leaves the register count to the compiler (2 blocks of 128
+// threads per SM); MinBlocks = 3 caps it for 3 blocks at a small spill cost.
+// The autotuner picks between them.
+template <int MinBlocks>
+__global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t n_items = pass_items(a);
   const unsigned long long budget = a.hdr->budget_ns;
@@ -34,7 +38,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
   uint32_t img = 0;
   bool active = false, drained = false;
   unsigned iter = 0;
-  unsigned long long w_max = 0;
+  unsigned long long w_max = 0, w_iters = 0, w_lanes = 0;
   unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_full = 0;
 
   const int pass = a.source;
@@ -66,10 +70,13 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
         mark_first(&a.hdr->t_pass[1][pass][a.level]);
       }
     }
-    if (__ballot_sync(kFull, active) == 0) {
+    const unsigned am = __ballot_sync(kFull, active);
+    if (am == 0) {
       if (__ballot_sync(kFull, !drained) == 0) break;
       continue;
     }
+    w_iters += 1ull;
+    w_lanes += (unsigned long long)__popc(am);
     if (active) {
       const int acc0 = r.nacc, rej0 = r.nrej;
       int term = ray_step64(*ip, m, r, a, item, img);
@@ -102,18 +109,27 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceArgs a) {
   flush_tally(&a.hdr->accepted, w_acc, lane);
   flush_tally(&a.hdr->rejected, w_rej, lane);
   flush_tally(&a.hdr->rays[a.level], w_rays, lane);
-  if (lane == 0) atomicMax(&a.hdr->t_pass[2][pass][a.level], globaltimer());
+  if (lane == 0) {
+    atomicMax(&a.hdr->t_pass[2][pass][a.level], globaltimer());
+    atomicAdd(&a.hdr->warp_iters[1], w_iters);
+    atomicAdd(&a.hdr->lane_iters[1], w_lanes);
+  }
   if (w_max) atomicMax(&a.hdr->max_ray_steps, w_max);
   flush_tally(&a.hdr->spill_full, w_full, lane);
 }
 
 cudaError_t launch_trace_fp64(const TraceArgs& a, LaunchShape s, cudaStream_t st) {
-  trace_fp64_kernel<<<s.blocks, s.threads, 0, st>>>(a);
+  if (s.variant == 1)
+    trace_fp64_kernel<3><<<s.blocks, s.threads, 0, st>>>(a);
+  else
+    trace_fp64_kernel<0><<<s.blocks, s.threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 size_t spill_record_bytes() { return sizeof(SpillRec); }
 
-const void* trace_fp64_kernel_ptr() { return (const void*)trace_fp64_kernel; }
+const void* trace_fp64_kernel_ptr(int variant) {
+  return variant == 1 ? (const void*)trace_fp64_kernel<3> : (const void*)trace_fp64_kernel<0>;
+}
 
 }  // namespace bhrt

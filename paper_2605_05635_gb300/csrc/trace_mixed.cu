@@ -317,7 +317,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     }
     dlt[i] = h * a5;
     float sc = c.atol + c.rtol * fmaxf(fabsf(r.yh[i]), fabsf(r.yh[i] + dlt[i]));
-    float q = h * ae / sc;
+    float q = __fdividef(h * ae, sc);
     err2 += q * q;
   }
   float err = sqrtf(err2 / 6.f);
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
   uint32_t img = 0;
   bool active = false, drained = false;
   unsigned iter = 0;
-  unsigned long long w_max = 0;
+  unsigned long long w_max = 0, w_iters = 0, w_lanes = 0;
   unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_promo = 0, w_full = 0;
 
   const int pass = (a.source ? 2 : 0);
@@ -458,10 +458,13 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
         mark_first(&a.hdr->t_pass[1][pass][a.level]);
       }
     }
-    if (__ballot_sync(kFull, active) == 0) {
+    const unsigned am = __ballot_sync(kFull, active);
+    if (am == 0) {
       if (__ballot_sync(kFull, !drained) == 0) break;
       continue;
     }
+    w_iters += 1ull;
+    w_lanes += (unsigned long long)__popc(am);
     if (active) {
       const int acc0 = r.nacc, rej0 = r.nrej;
       int term = ray_step_mx(*ip, mf, md, c, r, a, item, img, may_promote);
@@ -495,7 +498,11 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
   flush_tally(&a.hdr->accepted32, w_acc, lane);
   flush_tally(&a.hdr->rejected32, w_rej, lane);
   flush_tally(&a.hdr->rays[a.level], w_rays, lane);
-  if (lane == 0) atomicMax(&a.hdr->t_pass[2][pass][a.level], globaltimer());
+  if (lane == 0) {
+    atomicMax(&a.hdr->t_pass[2][pass][a.level], globaltimer());
+    atomicAdd(&a.hdr->warp_iters[0], w_iters);
+    atomicAdd(&a.hdr->lane_iters[0], w_lanes);
+  }
   if (w_max) atomicMax(&a.hdr->max_ray_steps, w_max);
   flush_tally(&a.hdr->promoted_rays, w_promo, lane);
   flush_tally(&a.hdr->spill_full, w_full, lane);
@@ -512,7 +519,7 @@ cudaError_t launch_trace_mixed(const TraceArgs& a, LaunchShape s, cudaStream_t s
 int trace_default_blocks_per_sm(int precision, int threads, int variant) {
   int nb = 0;
   if (precision == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_fp64_kernel_ptr(), threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_fp64_kernel_ptr(variant), threads, 0);
   else if (variant == 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel<4>, threads, 0);
   else

@@ -2,8 +2,10 @@
 isolation (``ncu ... python -m paper_2605_05635_gb300.profile_case``).
 
 Cases: ``kerr128`` (Kerr a = 0.5, i = 17 deg, 128^2 over [-10, 10]^2, no
-refinement) and ``sweep512`` (one 512^2 image of the six-image sweep, with
-refinement).
+refinement), ``sweep512`` (one 512^2 image of the six-image sweep, with
+refinement) and ``sweep512l0`` (the same image without refinement, so that
+the first trace launch carries all of the run's base rays).  The integrator
+settings are those of the chosen precision's sweep.
 """
 import argparse
 import math
@@ -16,15 +18,18 @@ from . import bhrt, workloads
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="kerr128", choices=["kerr128", "sweep512"])
+    ap.add_argument("--case", default="kerr128", choices=["kerr128", "sweep512", "sweep512l0"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--repeat", type=int, default=2)
     a = ap.parse_args(argv)
+    prec = bhrt.FP64 if a.precision == "fp64" else bhrt.MIXED
+    integ = workloads.FP64_INTEG if prec == bhrt.FP64 else workloads.MIXED_INTEG
     if a.case == "kerr128":
-        flat = dict(workloads.kerr_64(), nx=128, ny=128)
+        flat = dict(workloads.kerr_64(), nx=128, ny=128, **integ)
     else:
-        flat = workloads.sweep_512()[0]
-    flat["precision"] = bhrt.FP64 if a.precision == "fp64" else bhrt.MIXED
+        flat = dict(workloads.sweep_512()[0], **integ)
+        if a.case == "sweep512l0":
+            flat["levels"] = 0
     items = [bhrt.from_flat(flat)]
     plan = bhrt.Plan(items)
     for _ in range(a.repeat):
@@ -32,8 +37,11 @@ def main(argv=None):
     torch.cuda.synchronize()
     plan.check()
     st = plan.stats()
-    print(f"case {a.case} {a.precision}: rays {sum(st['rays'])} accepted fp32 "
-          f"{st['accepted_fp32']} fp64 {st['accepted_fp64']} promoted {st['promoted_rays']}")
+    print(f"case {a.case} {a.precision} (last launch): rays {sum(st['rays'])} accepted fp32 "
+          f"{st['accepted_fp32']} rejected fp32 {st['rejected_fp32']} fp64 "
+          f"{st['accepted_fp64']} rejected fp64 {st['rejected_fp64']} promoted "
+          f"{st['promoted_rays']} lane utilisation fp32 {st['lane_util_fp32']:.3f} "
+          f"fp64 {st['lane_util_fp64']:.3f}")
     plan.close()
 
 

@@ -71,6 +71,14 @@ def sweep_96(seed=20260513, n=256):
     return out
 
 
+def vis_1024(precision=1):
+    """One 1024^2 cored-NFW image (a = 0.94, i = 17 deg, +-12 M, 4x4
+    refinement to 3 levels): the input of the visibility benchmark."""
+    return dict(metric=CNFW, chi=0.94, incl=math.radians(17.0), r_obs=1000.0, nx=1024, ny=1024,
+                x_min=-12.0, x_max=12.0, y_min=-12.0, y_max=12.0, levels=3, **HALO[CNFW],
+                **EMISSION, **(MIXED_INTEG if precision == 1 else FP64_INTEG))
+
+
 def uv_points(k, seed, theta_g_muas=3.8, b_max_glambda=15.0):
     """k baselines with |b| ~ U(0, b_max) G-lambda and position angle
     ~ U(0, pi), returned as (u, v) in cycles per M: u = b theta_g."""
