@@ -84,16 +84,166 @@ struct MetricConsts {
   T eta_lc, lc, ilc;    // eta*lambda_c, lambda_c, 1/lambda_c
 };
 
-__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+
 __device__ __forceinline__ float d_exp(float x) { return __expf(x); }
-__device__ __forceinline__ double d_log1p(double x) { return log1p(x); }
-__device__ __forceinline__ float d_log1p(float x) { return log1pf(x); }
-__device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
-__device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+
+// FP32 log(1 + x) for x > -1 without a slow path: u = 1 + x = 2^e m with
+// m in [sqrt(1/2), sqrt(2)), log m = 2 atanh(t), t = (m - 1)/(m + 1),
+// |t| <= 0.172, by its series to t^9 (truncation below 3e-9), plus the
+// first-order correction for the rounding of 1 + x.
+__device__ __forceinline__ float d_log1p(float x) {
+  const float u = 1.0f + x;
+  const int ub = __float_as_int(u);
+  // biased exponent as a float: 2^23 + e_b read back, minus 2^23 + 127
+  float e = __int_as_float(0x4b000000 | ((ub >> 23) & 0xff)) - 8388735.0f;
+  float m = __int_as_float((ub & 0x007fffff) | 0x3f800000);  // [1, 2)
+  if (m > 1.41421356f) {
+    m *= 0.5f;
+    e += 1.0f;
+  }
+  const float t = __fdividef(m - 1.0f, m + 1.0f), t2 = t * t;
+  float p = fmaf(t2, 0.111111111f, 0.142857143f);          // 1/9, 1/7
+  p = fmaf(p, t2, 0.2f);                                    // 1/5
+  p = fmaf(p, t2, 0.333333333f);                            // 1/3
+  const float lm = 2.0f * fmaf(p * t2, t, t);
+  const float corr = __fdividef(x - (u - 1.0f), u);
+  return fmaf(e, 0.693147181f, lm + corr);                  // ln 2
+}
+// FP64 sine and cosine without a slow path, for the polar angle and trial
+// stages a few radians around it: Cody & Waite reduction by the nearest
+// multiple q of pi/2 with a two-part constant (exact to far below one unit
+// for |q| < 2^20), Taylor polynomials of sin r to r^19 and cos r to r^18 on
+// |r| <= pi/4 (truncation below 2e-21), then a rotation by q quarter turns;
+// q is rounded by adding 1.5 * 2^52, whose low mantissa bits hold q mod 4.
+__device__ __forceinline__ void d_sincos(double x, double* s, double* c) {
+  const double qm = fma(x, 0.63661977236758134308, 6755399441055744.0);
+  const double q = qm - 6755399441055744.0;
+  const int iq = (int)(unsigned)__double2loint(qm);
+  double r = fma(q, -1.5707963267948966192, x);            // pi/2, leading part
+  r = fma(q, -6.1232339957367660359e-17, r);               // pi/2, trailing part
+  const double r2 = r * r;
+  double ps = fma(r2, -8.22063524662433e-18, 2.8114572543455206e-15);  // -1/19!, 1/17!
+  ps = fma(ps, r2, -7.647163731819816e-13);  // -1/15!
+  ps = fma(ps, r2, 1.6059043836821613e-10);  // 1/13!
+  ps = fma(ps, r2, -2.505210838544172e-08);  // -1/11!
+  ps = fma(ps, r2, 2.7557319223985893e-06);  // 1/9!
+  ps = fma(ps, r2, -0.0001984126984126984);  // -1/7!
+  ps = fma(ps, r2, 0.008333333333333333);  // 1/5!
+  ps = fma(ps, r2, -0.16666666666666666);  // -1/3!
+  const double sr = fma(ps * r2, r, r);
+  double pc = fma(r2, -1.5619206968586225e-16, 4.779477332387385e-14);  // -1/18!, 1/16!
+  pc = fma(pc, r2, -1.1470745597729725e-11);  // -1/14!
+  pc = fma(pc, r2, 2.08767569878681e-09);  // 1/12!
+  pc = fma(pc, r2, -2.755731922398589e-07);  // -1/10!
+  pc = fma(pc, r2, 2.48015873015873e-05);  // 1/8!
+  pc = fma(pc, r2, -0.001388888888888889);  // -1/6!
+  pc = fma(pc, r2, 0.041666666666666664);  // 1/4!
+  pc = fma(pc, r2, -0.5);  // -1/2!
+  const double cr = fma(pc, r2, 1.0);
+  const double so = (iq & 1) ? cr : sr, co = (iq & 1) ? sr : cr;
+  *s = (iq & 2) ? -so : so;
+  *c = ((iq + 1) & 2) ? -co : co;
+}
+// FP32 sine and cosine without a slow path (the polar angle and the trial
+// stages around it stay within a few radians): Cody & Waite reduction by
+// the nearest multiple q of pi/2 with a two-part constant, Taylor
+// polynomials of sin r and cos r on |r| <= pi/4 (truncation below 2e-9),
+// then a rotation by q quarter turns.
+__device__ __forceinline__ void d_sincos(float x, float* s, float* c) {
+  // q = nearest integer to 2x/pi, rounded by adding 1.5 * 2^23 (its low
+  // mantissa bits then hold q mod 4), so no conversion instruction is needed
+  const float qm = fmaf(x, 0.636619772f, 12582912.0f);     // 2/pi, 1.5 * 2^23
+  const float q = qm - 12582912.0f;
+  const int iq = __float_as_int(qm);
+  float r = fmaf(q, -1.57079637f, x);                      // pi/2, leading part
+  r = fmaf(q, 4.37113883e-8f, r);                          // pi/2, trailing part
+  const float r2 = r * r;
+  float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
+  ps = fmaf(ps, r2, 8.33333333e-3f);                       // 1/5!
+  ps = fmaf(ps, r2, -1.66666667e-1f);                      // -1/3!
+  const float sr = fmaf(ps * r2, r, r);
+  float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);   // -1/10!, 1/8!
+  pc = fmaf(pc, r2, -1.38888889e-3f);                      // -1/6!
+  pc = fmaf(pc, r2, 4.16666667e-2f);                       // 1/4!
+  pc = fmaf(pc, r2, -0.5f);
+  const float cr = fmaf(pc, r2, 1.0f);
+  const float so = (iq & 1) ? cr : sr, co = (iq & 1) ? sr : cr;
+  *s = (iq & 2) ? -so : so;
+  *c = ((iq + 1) & 2) ? -co : co;
+}
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double d_rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float d_rcp(float x) { return __frcp_rn(x); }
+// FP64 reciprocal without a slow path: the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64) refined by two Newton steps r <- r + r (1 - x r),
+// within about one unit in the last place for the normal, finite x of the
+// right-hand side.
+__device__ __forceinline__ double d_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float d_rcp(float x) { return __fdividef(1.0f, x); }
+// FP64 exp without a slow path: x = k ln2 + r with k the nearest integer to
+// x / ln2 (rounded by adding 1.5 * 2^52) and r reduced by a two-part ln 2
+// (Cody & Waite), |r| <= ln2 / 2; e^r by its Taylor series to r^13
+// (truncation below 5e-18); 2^k assembled in the exponent field.  Results
+// below 2^-1022 flush to zero, above 2^1023 become +inf.
+__device__ __forceinline__ double d_exp(double x) {
+  if (!(x > -708.0)) return x != x ? x : 0.0;
+  if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+  const double km = fma(x, 1.4426950408889634074, 6755399441055744.0);  // 1/ln2, 1.5 * 2^52
+  const double k = km - 6755399441055744.0;
+  const int ik = (int)(unsigned)__double2loint(km);
+  double r = fma(k, -0.6931471805598903, x);   // ln 2, leading part
+  r = fma(k, -5.497923018708371e-14, r);          // ln 2, trailing part
+  double p = fma(r, 1.6059043836821613e-10, 2.08767569878681e-09);  // 1/13!, 1/12!
+  p = fma(p, r, 2.505210838544172e-08);  // 1/11!
+  p = fma(p, r, 2.755731922398589e-07);  // 1/10!
+  p = fma(p, r, 2.7557319223985893e-06);  // 1/9!
+  p = fma(p, r, 2.48015873015873e-05);  // 1/8!
+  p = fma(p, r, 0.0001984126984126984);  // 1/7!
+  p = fma(p, r, 0.001388888888888889);  // 1/6!
+  p = fma(p, r, 0.008333333333333333);  // 1/5!
+  p = fma(p, r, 0.041666666666666664);  // 1/4!
+  p = fma(p, r, 0.16666666666666666);  // 1/3!
+  p = fma(p, r, 0.5);  // 1/2!
+  p = fma(p, r, 1.0);  // 1/1!
+  p = fma(p, r, 1.0);  // 1/0!
+  return p * __longlong_as_double((long long)(ik + 1023) << 52);
+}
+
+// FP64 log(1 + x) for x > -1 without a slow path: u = 1 + x = 2^e m with m in
+// [sqrt(1/2), sqrt(2)); log m = 2 atanh(t), t = (m - 1)/(m + 1), |t| <= 0.172,
+// by its series to t^21 (truncation below 1e-18); e ln 2 with a two-part ln 2;
+// plus the first-order correction for the rounding of 1 + x.
+__device__ __forceinline__ double d_log1p(double x) {
+  const double u = 1.0 + x;
+  const long long ub = __double_as_longlong(u);
+  int e = (int)((ub >> 52) & 0x7ff) - 1023;
+  double m = __longlong_as_double((ub & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+  if (m > 1.4142135623730951) {
+    m *= 0.5;
+    e += 1;
+  }
+  const double t = (m - 1.0) * d_rcp(m + 1.0), t2 = t * t;
+  double p = fma(t2, 0.047619047619047616, 0.05263157894736842);  // 1/21, 1/19
+  p = fma(p, t2, 0.058823529411764705);  // 1/17
+  p = fma(p, t2, 0.06666666666666667);  // 1/15
+  p = fma(p, t2, 0.07692307692307693);  // 1/13
+  p = fma(p, t2, 0.09090909090909091);  // 1/11
+  p = fma(p, t2, 0.1111111111111111);  // 1/9
+  p = fma(p, t2, 0.14285714285714285);  // 1/7
+  p = fma(p, t2, 0.2);  // 1/5
+  p = fma(p, t2, 0.3333333333333333);  // 1/3
+  const double lm = 2.0 * fma(p * t2, t, t);
+  const double corr = (x - (u - 1.0)) * d_rcp(u);
+  const double ed = (double)e;
+  return fma(ed, 0.6931471805598903, fma(ed, 5.497923018708371e-14, lm + corr));
+}
+
 __device__ __forceinline__ double d_pow(double a, double b) { return pow(a, b); }
 __device__ __forceinline__ double d_tanh(double x) { return tanh(x); }
 

@@ -63,6 +63,39 @@ __device__ constexpr DPTabF kDPf = {
      BH_F(-1453857185.0 / 822651844.0), BH_F(69997945.0 / 29380423.0)}};
 #undef BH_F
 
+// The tableau in the order a rolled stage loop consumes it.  Once k_j is
+// known, stage j + 1 + u takes q[j][u] k_j into its running input sum
+// (u = 0..5), and the 5th-order update, the error estimate and the dense
+// output take b_j, e_j and d_j.  Each running sum adds its terms in
+// increasing j, as the unrolled sums do, so both forms round alike.  One
+// copy of the right-hand side then serves all six stages, which keeps the
+// stepping loop small enough for the instruction cache.
+template <class T>
+struct DPRolled {
+  T q[7][6];
+  T b[7];
+  T e[7];
+  T d[7];
+};
+
+template <class T, class Tab>
+constexpr DPRolled<T> make_rolled(const Tab& t) {
+  DPRolled<T> r{};
+  for (int j = 0; j < 7; ++j) {
+    for (int u = 0; u < 6; ++u) {
+      const int s = j + 1 + u;
+      r.q[j][u] = s <= 6 ? static_cast<T>(t.a[s][j]) : T(0);
+    }
+    r.b[j] = static_cast<T>(t.b[j]);
+    r.e[j] = static_cast<T>(t.e[j]);
+    r.d[j] = static_cast<T>(t.d[j]);
+  }
+  return r;
+}
+
+static __constant__ DPRolled<double> kDPr = make_rolled<double>(kDP);
+static __constant__ DPRolled<float> kDPrf = make_rolled<float>(kDPf);
+
 constexpr double kHalfPi = 1.57079632679489661923;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;
@@ -217,6 +250,27 @@ static __device__ __noinline__ void handle_crossing(const ImgParams& ip, const M
 }
 
 // FP64 ray state.
+// The FP64 right-hand side out of line, for the call sites that run once per
+// ray (launch, resume, axis reflection): the stepping loop keeps the only
+// inlined copy.
+struct RhsD {
+  double d[6];
+  double W, P2;
+};
+static __device__ __noinline__ RhsD rhs_f64(MetricConsts<double> m, double E, double ell,
+                                            double R, double th, double pR, double pth) {
+  RhsD o;
+  geo_rhs(m, E, ell, R, th, pR, pth, o.d, o.W, o.P2);
+  return o;
+}
+__device__ __forceinline__ void rhs_f64_into(const MetricConsts<double>& m, double E, double ell,
+                                             double R, double th, double pR, double pth,
+                                             double* d) {
+  const RhsD o = rhs_f64(m, E, ell, R, th, pR, pth);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d[i] = o.d[i];
+}
+
 struct Ray64 {
   double y[6];     // T, R, th, phi, p_R, p_th
   double f[6];     // f(y) (FSAL)
@@ -245,31 +299,33 @@ __device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricCons
   r.y[5] = ip.sq_gth * (-Y * id);
   r.ell = ip.sq_gph * (-X * id);
   r.E = ip.zamo_N + ip.zamo_w * r.ell;
-  double W, P2;
-  geo_rhs(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f, W, P2);
-  double d0 = 0, d1 = 0, sc[6];
+  rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
+  // starting-step heuristic in FP32 (it only needs a few digits)
+  float d0 = 0.f, d1 = 0.f, sc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    sc[i] = ip.atol + ip.rtol * fabs(r.y[i]);
-    d0 += (r.y[i] / sc[i]) * (r.y[i] / sc[i]);
-    d1 += (r.f[i] / sc[i]) * (r.f[i] / sc[i]);
+    sc[i] = (float)(ip.atol + ip.rtol * fabs(r.y[i]));
+    const float a0 = __fdividef((float)r.y[i], sc[i]), a1 = __fdividef((float)r.f[i], sc[i]);
+    d0 += a0 * a0;
+    d1 += a1 * a1;
   }
-  d0 = sqrt(d0 / 6.0);
-  d1 = sqrt(d1 / 6.0);
-  double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+  d0 = sqrtf(d0 / 6.f);
+  d1 = sqrtf(d1 / 6.f);
+  const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * __fdividef(d0, d1);
+  const double h0d = (double)h0;
   double f1[6];
-  geo_rhs(m, r.E, r.ell, r.y[1] + h0 * r.f[1], r.y[2] + h0 * r.f[2], r.y[4] + h0 * r.f[4],
-          r.y[5] + h0 * r.f[5], f1, W, P2);
-  double d2 = 0;
+  rhs_f64_into(m, r.E, r.ell, r.y[1] + h0d * r.f[1], r.y[2] + h0d * r.f[2],
+               r.y[4] + h0d * r.f[4], r.y[5] + h0d * r.f[5], f1);
+  float d2 = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double q = (f1[i] - r.f[i]) / sc[i];
+    const float q = __fdividef((float)(f1[i] - r.f[i]), sc[i]);
     d2 += q * q;
   }
-  d2 = sqrt(d2 / 6.0) / h0;
-  double mx = fmax(d1, d2);
-  double h1 = (mx <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / mx, 0.2);
-  r.h = fmin(100.0 * h0, h1);
+  d2 = __fdividef(sqrtf(d2 / 6.f), h0);
+  const float mx = fmaxf(d1, d2);
+  const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : exp2f(0.2f * log2f(0.01f / mx));
+  r.h = (double)fminf(100.f * h0, h1);
   r.lam = 0.0;
   r.cs.lam_last = 0.0;
   r.cs.have_trusted = false;
@@ -326,36 +382,54 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
                                           Ray64& r, const TraceArgs& a, int64_t item,
                                           uint32_t img) {
   const double h = r.h;
-  double k[7][6];
+  // rolled stage loop (see DPRolled): k is the latest stage derivative, q[u]
+  // the running input sums of the next stages, s5/se/sd the running sums of
+  // the update, the error estimate and the dense-output term; r.f keeps k_0
+  double k[6], q[6][6], s5[6], se[6], sd[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) k[0][i] = r.f[i];
+  for (int i = 0; i < 6; ++i) {
+    k[i] = r.f[i];
+    s5[i] = se[i] = sd[i] = 0.0;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) q[u][i] = 0.0;
+  }
   bool bad = false;
   double W = 0, P2oD = 1;
-#pragma unroll
-  for (int s = 1; s < 7; ++s) {
-    double ys[6];
+#pragma unroll 1
+  for (int j = 0; j < 7; ++j) {
+    const double bj = kDPr.b[j], ej = kDPr.e[j], dj = kDPr.d[j];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      double acc = 0.0;
-#pragma unroll
-      for (int j = 0; j < s; ++j) acc += kDP.a[s][j] * k[j][i];
-      ys[i] = r.y[i] + h * acc;
+      s5[i] = fma(bj, k[i], s5[i]);
+      se[i] = fma(ej, k[i], se[i]);
+      sd[i] = fma(dj, k[i], sd[i]);
     }
-    bool ok = geo_rhs(m, r.E, r.ell, ys[1], ys[2], ys[4], ys[5], k[s], W, P2oD);
+    if (j == 6) break;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const double c = kDPr.q[j][u];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) q[u][i] = fma(c, k[i], q[u][i]);
+    }
+    double ys[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ys[i] = r.y[i] + h * q[0][i];
+    bool ok = geo_rhs(m, r.E, r.ell, ys[1], ys[2], ys[4], ys[5], k, W, P2oD);
     bad |= !ok;
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) q[u][i] = q[u + 1][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q[5][i] = 0.0;
   }
   double y1[6];
   float err2 = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double a5 = 0.0, ae = 0.0;
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      a5 += kDP.b[j] * k[j][i];
-      ae += kDP.e[j] * k[j][i];
-    }
-    y1[i] = r.y[i] + h * a5;
-    err2 += err_term(r.y[i], y1[i], h * ae, ip.atol, ip.rtol);
+    y1[i] = r.y[i] + h * s5[i];
+    err2 += err_term(r.y[i], y1[i], h * se[i], ip.atol, ip.rtol);
   }
   float err = sqrtf(err2 / 6.f);
   r.steps++;
@@ -372,12 +446,9 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
       double hf0[6], hf1[6], hd[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        double a = 0.0;
-#pragma unroll
-        for (int j = 0; j < 7; ++j) a += kDP.d[j] * k[j][i];
-        hd[i] = h * a;
-        hf0[i] = h * k[0][i];
-        hf1[i] = h * k[6][i];
+        hd[i] = h * sd[i];
+        hf0[i] = h * r.f[i];
+        hf1[i] = h * k[i];
       }
       // copies: the ray state must not have its address taken (it would be
       // demoted from registers to local memory for every step)
@@ -394,12 +465,10 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     r.y[i] = y1[i];
-    r.f[i] = k[6][i];
+    r.f[i] = k[i];
   }
-  if (reflect_axis(r.y[2], r.y[5], r.y[3])) {
-    double Wr, Pr;
-    geo_rhs(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f, Wr, Pr);
-  }
+  if (reflect_axis(r.y[2], r.y[5], r.y[3]))
+    rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
   // null-constraint monitor at the new point (stage 7 = new point, FSAL)
   float hdv = (float)(fabs(W) / P2oD);
   if (hdv > r.hdrift) r.hdrift = hdv;
@@ -464,8 +533,7 @@ __device__ __forceinline__ void resume64(const SpillRec& s, const MetricConsts<d
   r.nacc = s.nacc;
   r.nrej = s.nrej;
   r.steps = s.steps;
-  double W, P2;
-  geo_rhs(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f, W, P2);
+  rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
 }
 
 // Resolves a fresh work item to its image, output pixel and screen point.

@@ -43,6 +43,26 @@ __device__ __forceinline__ void df_from(double x, float& hi, float& lo) {
 
 __device__ __forceinline__ double df_to(float hi, float lo) { return (double)hi + (double)lo; }
 
+// The right-hand side out of line, for the call sites that run once per ray
+// (launch, resume, axis reflection): the stepping loop keeps the only
+// inlined copy, so these do not grow the code the loop runs from.
+struct RhsF {
+  float d[6];
+  float W, P2;
+};
+static __device__ __noinline__ RhsF rhs_f32(MetricConsts<float> m, float E, float ell, float R,
+                                            float th, float pR, float pth) {
+  RhsF o;
+  geo_rhs(m, E, ell, R, th, pR, pth, o.d, o.W, o.P2);
+  return o;
+}
+__device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, float E, float ell,
+                                             float R, float th, float pR, float pth, float* d) {
+  const RhsF o = rhs_f32(m, E, ell, R, th, pR, pth);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d[i] = o.d[i];
+}
+
 struct RayMx {
   float yh[6], yl[6];  // state T, R, th, phi, p_R, p_th as hi + lo
   float f[6];          // f(y) in FP32 (FSAL)
@@ -118,8 +138,7 @@ __device__ __forceinline__ void mx_resume(const SpillRec& s, const MetricConsts<
   x.nacc = s.nacc;
   x.nrej = s.nrej;
   x.steps = s.steps;
-  float W, P2;
-  geo_rhs(mf, x.Ef, x.ellf, x.yh[1], x.yh[2], x.yh[4], x.yh[5], x.f, W, P2);
+  rhs_f32_into(mf, x.Ef, x.ellf, x.yh[1], x.yh[2], x.yh[4], x.yh[5], x.f);
 }
 
 struct MxConsts {
@@ -143,8 +162,7 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   df_from(ip.sq_gth * (-Y * id), r.yh[5], r.yl[5]);
   r.Ef = (float)r.E;
   r.ellf = (float)r.ell;
-  float W, P2;
-  geo_rhs(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f, W, P2);
+  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f);
   float d0 = 0.f, d1 = 0.f, sc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -156,8 +174,8 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   d1 = sqrtf(d1 / 6.f);
   const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * d0 / d1;
   float f1[6];
-  geo_rhs(mf, r.Ef, r.ellf, r.yh[1] + h0 * r.f[1], r.yh[2] + h0 * r.f[2], r.yh[4] + h0 * r.f[4],
-          r.yh[5] + h0 * r.f[5], f1, W, P2);
+  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1] + h0 * r.f[1], r.yh[2] + h0 * r.f[2],
+               r.yh[4] + h0 * r.f[4], r.yh[5] + h0 * r.f[5], f1);
   float d2 = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -284,41 +302,59 @@ constexpr float kPiHi = 3.1415927410125732421875f;
 // One attempted FP32 step.  Returns 0 (continue), terminal status + 1, or 4
 // when the ray must be promoted to FP64.
 __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricConsts<float>& mf,
-                                           const MetricConsts<double>& md, const MxConsts& c,
+                                           const MxConsts& c,
                                            RayMx& r, const TraceArgs& a, int64_t item,
                                            uint32_t img, bool may_promote) {
   const float h = r.h;
-  float k[7][6];
+  // k: the latest stage derivative; q[u]: running input sums of the next
+  // stages; s5, se, sd: running sums of the update, the error estimate and
+  // the dense-output term (see DPRolled).  r.f keeps k_0 until the end.
+  float k[6], q[6][6], s5[6], se[6], sd[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) k[0][i] = r.f[i];
+  for (int i = 0; i < 6; ++i) {
+    k[i] = r.f[i];
+    s5[i] = se[i] = sd[i] = 0.f;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) q[u][i] = 0.f;
+  }
   bool bad = false;
   float W = 0.f, P2oD = 1.f;
-#pragma unroll
-  for (int s = 1; s < 7; ++s) {
-    float ys[6];
+#pragma unroll 1
+  for (int j = 0; j < 7; ++j) {
+    const float bj = kDPrf.b[j], ej = kDPrf.e[j], dj = kDPrf.d[j];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < s; ++j) acc += kDPf.a[s][j] * k[j][i];
-      ys[i] = r.yh[i] + (r.yl[i] + h * acc);
+      s5[i] = fmaf(bj, k[i], s5[i]);
+      se[i] = fmaf(ej, k[i], se[i]);
+      sd[i] = fmaf(dj, k[i], sd[i]);
     }
-    bool ok = geo_rhs(mf, r.Ef, r.ellf, ys[1], ys[2], ys[4], ys[5], k[s], W, P2oD);
+    if (j == 6) break;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const float c = kDPrf.q[j][u];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) q[u][i] = fmaf(c, k[i], q[u][i]);
+    }
+    float ys[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ys[i] = r.yh[i] + (r.yl[i] + h * q[0][i]);
+    bool ok = geo_rhs(mf, r.Ef, r.ellf, ys[1], ys[2], ys[4], ys[5], k, W, P2oD);
     bad |= !ok;
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) q[u][i] = q[u + 1][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q[5][i] = 0.f;
   }
   float dlt[6], err2 = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    float a5 = 0.f, ae = 0.f;
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      a5 += kDPf.b[j] * k[j][i];
-      ae += kDPf.e[j] * k[j][i];
-    }
-    dlt[i] = h * a5;
+    dlt[i] = h * s5[i];
     float sc = c.atol + c.rtol * fmaxf(fabsf(r.yh[i]), fabsf(r.yh[i] + dlt[i]));
-    float q = __fdividef(h * ae, sc);
-    err2 += q * q;
+    float qe = __fdividef(h * se[i], sc);
+    err2 += qe * qe;
   }
   float err = sqrtf(err2 / 6.f);
   r.steps++;
@@ -344,14 +380,11 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
       float y0h[6], y0l[6], hf0[6], hf1[6], hd[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        float acc = 0.f;
-#pragma unroll
-        for (int j = 0; j < 7; ++j) acc += kDPf.d[j] * k[j][i];
         y0h[i] = r.yh[i];
         y0l[i] = r.yl[i];
-        hd[i] = h * acc;
-        hf0[i] = h * k[0][i];
-        hf1[i] = h * k[6][i];
+        hd[i] = h * sd[i];
+        hf0[i] = h * r.f[i];
+        hf1[i] = h * k[i];
       }
       CrossState cs = r.cs;  // copies keep the ray state in registers
       const CrossOut co = cross_out(a, item, img);
@@ -365,7 +398,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   for (int i = 0; i < 6; ++i) {
     r.yh[i] = nh[i];
     r.yl[i] = nl[i];
-    r.f[i] = k[6][i];
+    r.f[i] = k[i];
   }
   // polar axis (see reflect_axis): theta -> -theta or 2 pi - theta,
   // p_th -> -p_th, phi -> phi + pi
@@ -377,8 +410,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
       df_from(th, r.yh[2], r.yl[2]);
       df_from(pth, r.yh[5], r.yl[5]);
       df_from(ph, r.yh[3], r.yl[3]);
-      float Wr, Pr;
-      geo_rhs(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f, Wr, Pr);
+      rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f);
     }
   }
   float hdv = fabsf(W) / P2oD;
@@ -408,7 +440,6 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
 
   RayMx r;
   MetricConsts<float> mf;
-  MetricConsts<double> md;
   MxConsts c;
   const ImgParams* ip = a.ip;
   int64_t item = -1;
@@ -431,7 +462,6 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
           img = s.img;
           ip = &a.ip[img];
           mf = metric_consts<float>(*ip);
-          md = metric_consts<double>(*ip);
           mx_resume(s, mf, r);
         } else {
           double X, Y;
@@ -440,7 +470,6 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
           resolve_item(a, idx, img, pix, X, Y);
           ip = &a.ip[img];
           mf = metric_consts<float>(*ip);
-          md = metric_consts<double>(*ip);
           c.rtol = (float)fmax(ip->rtol, 1e-9);  // FP32 noise floor of the estimate
           c.atol = (float)ip->atol;
           ray_init_mx(*ip, mf, c, X, Y, r);
@@ -467,7 +496,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
     w_lanes += (unsigned long long)__popc(am);
     if (active) {
       const int acc0 = r.nacc, rej0 = r.nrej;
-      int term = ray_step_mx(*ip, mf, md, c, r, a, item, img, may_promote);
+      int term = ray_step_mx(*ip, mf, c, r, a, item, img, may_promote);
       w_acc += (unsigned long long)(r.nacc - acc0);
       w_rej += (unsigned long long)(r.nrej - rej0);
       if (term == 4) {

@@ -24,9 +24,11 @@ EMISSION = dict(r_in_mode=0, j0=1.0, p=2.0, R_s=8.0, sigma_in=0.2, sigma_out=2.0
 FP64_INTEG = dict(precision=0, rtol=1e-10, atol=1e-12, max_steps=1_000_000, cap_factor=1.01,
                   esc_factor=1.1, thetadot_min=1e-8, dlambda_min=1e-6, promote_dr=0.1)
 
-# Mixed path: FP32 bulk with FP64 promotion; its step tolerance sits above
-# the FP32 round-off floor of the error estimate.
-MIXED_INTEG = dict(FP64_INTEG, precision=1, rtol=1e-8, atol=1e-10)
+# Mixed path: FP32 bulk with FP64 promotion; its step tolerances sit above
+# the FP32 round-off floor of the error estimate (an absolute tolerance
+# below about 1e-8 only adds rejected steps where a component passes
+# through zero, without changing the images).
+MIXED_INTEG = dict(FP64_INTEG, precision=1, rtol=1e-8, atol=1e-8)
 
 
 def kerr_64():

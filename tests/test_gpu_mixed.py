@@ -4,7 +4,8 @@ the FP64 oracle.
 Bar: intensity within 1e-4 of the image maximum; integer planes exact except
 on rays whose class is not determined at the mixed path's precision (the
 oracle's own class changes under a relative screen perturbation of 1e-6 or
-when its tolerance moves among the mixed path's 1e-8, 1e-10 and 1e-12).
+when its tolerances move among the mixed path's (rtol, atol) = (1e-8, 1e-8)
+and (1e-8, 1e-10), (1e-10, 1e-12), (1e-12, 1e-14)).
 """
 import math
 
@@ -34,8 +35,8 @@ def class_sensitive(oracle, flat, X, Y, eps=1e-6):
     d = eps * max(abs(X), abs(Y), 1.0)
     pts += [[X + d, Y], [X - d, Y], [X, Y + d], [X, Y - d]]
     classes = set()
-    for rtol in (1e-8, 1e-10, 1e-12):
-        P = oracle.problem(**{**base, "rtol": rtol, "atol": rtol * 1e-2})
+    for rtol, atol in ((1e-8, 1e-8), (1e-8, 1e-10), (1e-10, 1e-12), (1e-12, 1e-14)):
+        P = oracle.problem(**{**base, "rtol": rtol, "atol": atol})
         for r in oracle.trace_points(P, pts):
             classes.add((int(r["status"]), int(r["ncross"])))
     return len(classes) > 1
