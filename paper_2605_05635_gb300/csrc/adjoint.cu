@@ -132,7 +132,7 @@ __device__ int adj_step(const ImgParams& ip, const MetricConsts<double>& m, Ray6
       ae += kDP.e[j] * k[j][i];
     }
     y1[i] = r.y[i] + h * a5;
-    err2 += err_term(r.y[i], y1[i], h * ae, ip.atol, ip.rtol);
+    err2 += err_term(r.y[i], y1[i], h * ae, f32_trunc(ip.atol), f32_trunc(ip.rtol));
   }
   float err = sqrtf(err2 / 6.f);
   r.steps++;

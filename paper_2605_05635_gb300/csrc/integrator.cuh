@@ -76,19 +76,29 @@ struct DPRolled {
   T b[7];
   T e[7];
   T d[7];
+  // nonzero coefficients as bit masks (integer tests, so that skipping a
+  // zero term costs no floating-point compare): bit u of qmask[j] for
+  // q[j][u]; bit j of bmask, emask, dmask
+  int qmask[7];
+  int bmask, emask, dmask;
 };
 
 template <class T, class Tab>
 constexpr DPRolled<T> make_rolled(const Tab& t) {
   DPRolled<T> r{};
   for (int j = 0; j < 7; ++j) {
+    r.qmask[j] = 0;
     for (int u = 0; u < 6; ++u) {
       const int s = j + 1 + u;
       r.q[j][u] = s <= 6 ? static_cast<T>(t.a[s][j]) : T(0);
+      if (r.q[j][u] != T(0)) r.qmask[j] |= 1 << u;
     }
     r.b[j] = static_cast<T>(t.b[j]);
     r.e[j] = static_cast<T>(t.e[j]);
     r.d[j] = static_cast<T>(t.d[j]);
+    if (r.b[j] != T(0)) r.bmask |= 1 << j;
+    if (r.e[j] != T(0)) r.emask |= 1 << j;
+    if (r.d[j] != T(0)) r.dmask |= 1 << j;
   }
   return r;
 }
@@ -368,13 +378,26 @@ __device__ __forceinline__ CrossOut cross_out(const TraceArgs& a, int64_t item, 
 
 // One attempted FP64 step.  Returns 0 while the ray continues, else the
 // terminal status + 1 (1 escaped, 2 captured, 3 undetermined).
-// One component's squared scaled error (h e_i / sc_i)^2 with the scale
-// sc_i = atol + rtol max(|y0_i|, |y1_i|) in FP64 and the ratio in FP32: the
-// norm only decides acceptance and the next step factor, to a few digits.
-__device__ __forceinline__ float err_term(double y0, double y1, double he, double atol,
-                                          double rtol) {
-  const double sc = atol + rtol * fmax(fabs(y0), fabs(y1));
-  const float q = __fdividef((float)he, (float)sc);
+// A double truncated to FP32 precision by bit manipulation on the integer
+// pipes (no FP64-pipe conversion): the exponent rebiased, the leading 20
+// mantissa bits kept; magnitudes below 2^-126 give 0, above 2^128 the largest
+// float.  Relative error below 2^-20.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 896;  // rebias 1023 -> 127
+  const int sign = hi & (int)0x80000000;
+  const int mag = e <= 0 ? 0 : (e >= 255 ? 0x7f7fffff : ((e << 23) | ((hi & 0xfffff) << 3)));
+  return __int_as_float(sign | mag);
+}
+
+// One component's squared scaled error (h e_i / sc_i)^2,
+// sc_i = atol + rtol max(|y0_i|, |y1_i|), in FP32 from truncated operands:
+// the norm only decides acceptance and the next step factor, to a few
+// digits, and the FP64 pipe is the FP64 step's bottleneck.
+__device__ __forceinline__ float err_term(double y0, double y1, double he, float atol,
+                                          float rtol) {
+  const float sc = fmaf(rtol, fmaxf(fabsf(f32_trunc(y0)), fabsf(f32_trunc(y1))), atol);
+  const float q = __fdividef(f32_trunc(he), sc);
   return q * q;
 }
 
@@ -397,19 +420,32 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   double W = 0, P2oD = 1;
 #pragma unroll 1
   for (int j = 0; j < 7; ++j) {
-    const double bj = kDPr.b[j], ej = kDPr.e[j], dj = kDPr.d[j];
+    // zero coefficients (about a third of the triangular sums) are skipped
+    // by uniform integer tests: FP64 operations are the pass's bottleneck
+    if ((kDPr.bmask >> j) & 1) {
+      const double bj = kDPr.b[j];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      s5[i] = fma(bj, k[i], s5[i]);
-      se[i] = fma(ej, k[i], se[i]);
-      sd[i] = fma(dj, k[i], sd[i]);
+      for (int i = 0; i < 6; ++i) s5[i] = fma(bj, k[i], s5[i]);
+    }
+    if ((kDPr.emask >> j) & 1) {
+      const double ej = kDPr.e[j];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) se[i] = fma(ej, k[i], se[i]);
+    }
+    if ((kDPr.dmask >> j) & 1) {
+      const double dj = kDPr.d[j];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sd[i] = fma(dj, k[i], sd[i]);
     }
     if (j == 6) break;
+    const int qm = kDPr.qmask[j];
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
-      const double c = kDPr.q[j][u];
+      if ((qm >> u) & 1) {
+        const double c = kDPr.q[j][u];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) q[u][i] = fma(c, k[i], q[u][i]);
+        for (int i = 0; i < 6; ++i) q[u][i] = fma(c, k[i], q[u][i]);
+      }
     }
     double ys[6];
 #pragma unroll
@@ -426,10 +462,11 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   }
   double y1[6];
   float err2 = 0.f;
+  const float fatol = f32_trunc(ip.atol), frtol = f32_trunc(ip.rtol);
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     y1[i] = r.y[i] + h * s5[i];
-    err2 += err_term(r.y[i], y1[i], h * se[i], ip.atol, ip.rtol);
+    err2 += err_term(r.y[i], y1[i], h * se[i], fatol, frtol);
   }
   float err = sqrtf(err2 / 6.f);
   r.steps++;

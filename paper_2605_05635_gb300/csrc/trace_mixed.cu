@@ -321,6 +321,9 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   float W = 0.f, P2oD = 1.f;
 #pragma unroll 1
   for (int j = 0; j < 7; ++j) {
+    // all coefficients, zeros included: branching around the zero terms
+    // (as the FP64 step does) costs the issue-bound FP32 loop more than the
+    // FMAs it saves
     const float bj = kDPrf.b[j], ej = kDPrf.e[j], dj = kDPrf.d[j];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
