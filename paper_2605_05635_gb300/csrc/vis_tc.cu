@@ -9,16 +9,18 @@
 //   Im V_k = -sum_j [sin(2 pi v_k Y_j) C_kj + cos(2 pi v_k Y_j) S_kj] dX dY.
 // Precision: both operands are split into hi + lo parts in BF16 (or FP16)
 // and the three significant products hi*hi + hi*lo + lo*hi are accumulated in
-// FP32 in tensor memory, by concatenating along the reduction axis:
-//   A' = [A_hi | A_hi | A_lo],  B' = [B_hi | B_lo | B_hi].
+// FP32 in tensor memory.
 //
 // One CTA owns 64 baselines (128 accumulator rows: 64 cos + 64 sin) and
-// sweeps the image rows in passes of 512 columns of tensor memory.  Phase
-// tiles of A' are generated on chip straight into shared memory in the
-// 128-byte-swizzled K-major layout; image tiles of B' arrive by TMA in the
-// same layout.  Two pipeline stages overlap phase generation and TMA with the
-// MMAs of the previous chunk.  The epilogue reads the accumulators with
-// tcgen05.ld, applies the v-phases and reduces over j.
+// sweeps the image rows in passes of 256 columns of tensor memory.  For each
+// 64-column chunk of the reduction axis the CTA generates the phase tile once,
+// on chip, straight into shared memory as its hi and lo parts in the
+// 128-byte-swizzled K-major layout (a sincospif every 16 columns and a
+// rotation recurrence between), while TMA brings the hi and lo parts of the
+// image tile; one thread then issues the three products of the chunk.  Two
+// pipeline stages overlap phase generation and TMA with the MMAs of the
+// previous chunk.  The epilogue reads the accumulators with tcgen05.ld,
+// applies the v-phases (the same recurrence) and reduces over j.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -34,13 +36,15 @@ namespace bhrt {
 constexpr int kVisRows = 128;       // accumulator lanes (64 baselines x cos/sin)
 constexpr int kVisUV = 64;          // baselines per CTA
 constexpr int kVisKC = 64;          // reduction chunk (elements): 128 bytes of 16-bit
-constexpr int kVisNP = 512;         // image rows per pass (TMEM columns)
+constexpr int kVisNP = 256;         // image rows per pass (TMEM columns)
 constexpr int kVisThreads = 256;
 constexpr int kStages = 2;
-constexpr int kAStage = kVisRows * kVisKC * 2;   // 16 KB
-constexpr int kBStage = kVisNP * kVisKC * 2;     // 64 KB
+constexpr int kATile = kVisRows * kVisKC * 2;    // 16 KB: one part (hi or lo) of A
+constexpr int kBTile = kVisNP * kVisKC * 2;      // 32 KB: one part of B
+constexpr int kStage = 2 * kATile + 2 * kBTile;  // 96 KB: A hi, A lo, B hi, B lo
 constexpr int kVisMaxNx = 4096;    // bound of the per-CTA phase table
-constexpr int kVisSmem = kStages * (kAStage + kBStage) + 1024 + 256 + 2048 +
+constexpr int kSeg = 16;            // columns per thread between sincospif reseeds
+constexpr int kVisSmem = kStages * kStage + 1024 + 256 + 2048 +
                          kVisUV * (kVisMaxNx / kVisKC) * 4;
 constexpr unsigned kSpinLimit = 1u << 26;
 
@@ -152,7 +156,7 @@ __device__ __forceinline__ void split16(float v, bool fp16, uint16_t& hi, uint16
   }
 }
 
-// Image -> B' = [hi | lo | hi] rows of length 3 * nxp (zero padded).
+// Image -> B2 = [hi | lo] rows of length 2 * nxp (zero padded).
 __global__ void vis_prepare_image(const float* I, VisArgs a, uint16_t* Bp) {
   const int64_t n = (int64_t)a.ny * a.nxp;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
@@ -161,10 +165,9 @@ __global__ void vis_prepare_image(const float* I, VisArgs a, uint16_t* Bp) {
     float v = i < a.nx ? (float)((double)I[(int64_t)j * a.nx + i] * a.scale) : 0.f;
     uint16_t hi, lo;
     split16(v, a.fp16 != 0, hi, lo);
-    uint16_t* row = Bp + (int64_t)j * 3 * a.nxp;
+    uint16_t* row = Bp + (int64_t)j * 2 * a.nxp;
     row[i] = hi;
     row[a.nxp + i] = lo;
-    row[2 * a.nxp + i] = hi;
   }
 }
 
@@ -173,9 +176,7 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* sA = smem;                                // [stages][16 KB]
-  unsigned char* sB = smem + kStages * kAStage;            // [stages][64 KB]
-  uint64_t* bar_full = reinterpret_cast<uint64_t*>(sB + kStages * kBStage);  // TMA landed
+  uint64_t* bar_full = reinterpret_cast<uint64_t*>(smem + kStages * kStage);  // TMA landed
   uint64_t* bar_mma = bar_full + kStages;                  // MMAs of a stage done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_mma + kStages);
   int* fail = reinterpret_cast<int*>(tmem_slot + 1);       // CTA-uniform failure flag
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(512));
+                 "r"(kVisNP));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -205,23 +206,24 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
 
-  // per-thread baseline constants for phase generation: this thread fills
-  // rows r (cos) and r + 64 (sin) for baseline kk = tid % 64, columns
-  // tid / 64 + 4 q of each chunk.
+  // phase generation: this thread fills rows kk (cos) and kk + 64 (sin) for
+  // baseline kk = tid % 64, columns seg * 16 .. seg * 16 + 15 of each chunk
   const int kk = tid & 63;
-  const int col0 = tid >> 6;              // 0..3
+  const int seg = tid >> 6;                // 0..3
   const int64_t kidx = uv0 + kk;
   const double u = kidx < a.K ? a.uv[2 * kidx] : 0.0;
   const float two_u_dx = (float)(2.0 * u * a.dx);
-  // phase table: 2 u X_{64 b} reduced mod 2, once per CTA in FP64
+  float rot_s, rot_c;                      // one column step of the u-phase
+  sincospif(two_u_dx, &rot_s, &rot_c);
+  // phase table: 2 u X at the first column of each chunk, reduced mod 2, in FP64
   const int nblk = a.nxp / kVisKC;
-  for (int b = col0; b < nblk; b += 4) {
+  for (int b = seg; b < nblk; b += 4) {
     double t = 2.0 * u * (a.x_min + (kVisKC * b + 0.5) * a.dx);
     tbase[kk * nblk + b] = (float)(t - 2.0 * rint(0.5 * t));
   }
   __syncthreads();
 
-  const int chunks = 3 * a.nxp / kVisKC;
+  const int chunks = nblk;
   const int passes = (a.ny + kVisNP - 1) / kVisNP;
   const uint32_t idesc = instr_desc(fp16);
   bool ok = true;
@@ -229,13 +231,20 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   // epilogue accumulators for the thread's (row, column-half): P = sum c D, Q = sum s D
   float accP = 0.f, accQ = 0.f;
   const int erow = (warp & 3) * 32 + lane;          // TMEM lane this thread reads
-  const int ehalf = warp >> 2;                      // which 256-column half
+  const int ehalf = warp >> 2;                      // which 128-column half
   const int64_t ek = uv0 + (erow & 63);
   const double ev = ek < a.K ? a.uv[2 * ek + 1] : 0.0;
+  const float dv = (float)(2.0 * ev * a.dy);
+  float vrot_s, vrot_c;
+  sincospif(dv, &vrot_s, &vrot_c);
 
   for (int pass = 0; pass < passes && ok; ++pass) {
     for (int c = 0; c < chunks && ok; ++c) {
       const int s = (pass * chunks + c) % kStages;
+      unsigned char* sAh = smem + s * kStage;
+      unsigned char* sAl = sAh + kATile;
+      unsigned char* sBh = sAl + kATile;
+      unsigned char* sBl = sBh + kBTile;
       // wait (one thread, bounded) for the MMAs that last used this stage
       if (tid == 0 && use[s] > 0 && !mbar_wait(&bar_mma[s], (use[s] - 1) & 1)) *fail = 1;
       __syncthreads();
@@ -244,34 +253,55 @@ __global__ void __launch_bounds__(kVisThreads, 1)
         break;
       }
       if (tid == 0) {
-        mbar_expect_tx(&bar_full[s], kBStage);
-        tma_load_2d(sB + s * kBStage, &bmap, c * kVisKC, pass * kVisNP, &bar_full[s]);
-        tma_load_2d(sB + s * kBStage + kBStage / 2, &bmap, c * kVisKC, pass * kVisNP + 256,
-                    &bar_full[s]);
+        mbar_expect_tx(&bar_full[s], 2 * kBTile);
+        tma_load_2d(sBh, &bmap, c * kVisKC, pass * kVisNP, &bar_full[s]);
+        tma_load_2d(sBl, &bmap, a.nxp + c * kVisKC, pass * kVisNP, &bar_full[s]);
       }
-      // phase tile of A': third t of the reduction axis
-      const int kg = c * kVisKC;
-      const int third = kg / a.nxp;
-      const int i0 = kg - third * a.nxp;
-      const bool want_lo = third == 2;
-      // base argument 2 u X_{i0} (mod 2) from the table, increments in FP32
-      const float t0 = tbase[kk * nblk + i0 / kVisKC];
-      unsigned char* At = sA + s * kAStage;
-#pragma unroll 4
-      for (int q = 0; q < kVisKC / 4; ++q) {
-        const int col = col0 + 4 * q;
-        float arg = t0 + (float)col * two_u_dx;
+      // phase tile, hi and lo parts: a sincospif at the segment start, then
+      // rotations by one column step (16 steps at most between reseeds)
+      {
+        const float t0 = tbase[kk * nblk + c] + (float)(seg * kSeg) * two_u_dx;
         float sn, cs;
-        sincospif(arg, &sn, &cs);
-        uint16_t ch, cl, sh, sl;
-        split16(cs, fp16, ch, cl);
-        split16(sn, fp16, sh, sl);
-        const uint16_t cv = want_lo ? cl : ch, sv = want_lo ? sl : sh;
-        // 128-byte swizzle: 16-byte chunk index (col / 8) xor (row % 8)
-        const int chunk16 = col >> 3, within = (col & 7) * 2;
+        sincospif(t0, &sn, &cs);
+        uint16_t ch[kSeg], cl[kSeg], sh[kSeg], sl[kSeg];
+#pragma unroll
+        for (int q = 0; q < kSeg; ++q) {
+          split16(cs, fp16, ch[q], cl[q]);
+          split16(sn, fp16, sh[q], sl[q]);
+          const float cn = fmaf(cs, rot_c, -sn * rot_s);
+          sn = fmaf(sn, rot_c, cs * rot_s);
+          cs = cn;
+        }
+        // 128-byte swizzle: 16-byte chunk (col / 8) xor (row % 8); this
+        // thread's 16 columns are chunks 2 seg and 2 seg + 1 of its rows
         const int r0 = kk, r1 = kk + 64;
-        *reinterpret_cast<uint16_t*>(At + r0 * 128 + ((chunk16 ^ (r0 & 7)) << 4) + within) = cv;
-        *reinterpret_cast<uint16_t*>(At + r1 * 128 + ((chunk16 ^ (r1 & 7)) << 4) + within) = sv;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int ch16 = 2 * seg + h;
+          uint4 vch, vcl, vsh, vsl;
+          vch.x = ch[8 * h + 0] | ((uint32_t)ch[8 * h + 1] << 16);
+          vch.y = ch[8 * h + 2] | ((uint32_t)ch[8 * h + 3] << 16);
+          vch.z = ch[8 * h + 4] | ((uint32_t)ch[8 * h + 5] << 16);
+          vch.w = ch[8 * h + 6] | ((uint32_t)ch[8 * h + 7] << 16);
+          vcl.x = cl[8 * h + 0] | ((uint32_t)cl[8 * h + 1] << 16);
+          vcl.y = cl[8 * h + 2] | ((uint32_t)cl[8 * h + 3] << 16);
+          vcl.z = cl[8 * h + 4] | ((uint32_t)cl[8 * h + 5] << 16);
+          vcl.w = cl[8 * h + 6] | ((uint32_t)cl[8 * h + 7] << 16);
+          vsh.x = sh[8 * h + 0] | ((uint32_t)sh[8 * h + 1] << 16);
+          vsh.y = sh[8 * h + 2] | ((uint32_t)sh[8 * h + 3] << 16);
+          vsh.z = sh[8 * h + 4] | ((uint32_t)sh[8 * h + 5] << 16);
+          vsh.w = sh[8 * h + 6] | ((uint32_t)sh[8 * h + 7] << 16);
+          vsl.x = sl[8 * h + 0] | ((uint32_t)sl[8 * h + 1] << 16);
+          vsl.y = sl[8 * h + 2] | ((uint32_t)sl[8 * h + 3] << 16);
+          vsl.z = sl[8 * h + 4] | ((uint32_t)sl[8 * h + 5] << 16);
+          vsl.w = sl[8 * h + 6] | ((uint32_t)sl[8 * h + 7] << 16);
+          const int o0 = r0 * 128 + ((ch16 ^ (r0 & 7)) << 4);
+          const int o1 = r1 * 128 + ((ch16 ^ (r1 & 7)) << 4);
+          *reinterpret_cast<uint4*>(sAh + o0) = vch;
+          *reinterpret_cast<uint4*>(sAl + o0) = vcl;
+          *reinterpret_cast<uint4*>(sAh + o1) = vsh;
+          *reinterpret_cast<uint4*>(sAl + o1) = vsl;
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -280,15 +310,16 @@ __global__ void __launch_bounds__(kVisThreads, 1)
           *fail = 1;
         } else {
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t aaddr = smem_u32(At), baddr = smem_u32(sB + s * kBStage);
+          const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh),
+                         bl = smem_u32(sBl);
 #pragma unroll
-          for (int kk16 = 0; kk16 < kVisKC / 16; ++kk16) {
-            const uint64_t ad = smem_desc_sw128(aaddr + kk16 * 32);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint64_t bd = smem_desc_sw128(baddr + h * (kBStage / 2) + kk16 * 32);
-              mma_f16(tmem + h * 256, ad, bd, idesc, c > 0 || kk16 > 0);
-            }
+          for (int k16 = 0; k16 < kVisKC / 16; ++k16) {
+            const uint32_t off = k16 * 32;
+            const uint64_t dah = smem_desc_sw128(ah + off), dal = smem_desc_sw128(al + off);
+            const uint64_t dbh = smem_desc_sw128(bh + off), dbl = smem_desc_sw128(bl + off);
+            mma_f16(tmem, dah, dbh, idesc, c > 0 || k16 > 0);   // hi x hi
+            mma_f16(tmem, dah, dbl, idesc, true);               // hi x lo
+            mma_f16(tmem, dal, dbh, idesc, true);               // lo x hi
           }
           mma_commit(&bar_mma[s]);
         }
@@ -307,13 +338,11 @@ __global__ void __launch_bounds__(kVisThreads, 1)
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const double tvp = 2.0 * ev * (a.y_min + (pass * kVisNP + ehalf * 256 + 0.5) * a.dy);
-    const float tv0 = (float)(tvp - 2.0 * rint(0.5 * tvp));
-    const float dv = (float)(2.0 * ev * a.dy);
-    // epilogue: this thread reads lane erow, columns ehalf*256 .. +256
-    for (int cb = 0; cb < 256; cb += 16) {
+    // epilogue: this thread reads lane erow, columns ehalf * 128 .. + 128
+    const int jcol0 = pass * kVisNP + ehalf * 128;
+    for (int cb = 0; cb < 128; cb += 16) {
       uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ehalf * 256 + cb);
+      const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ehalf * 128 + cb);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
           "%13,%14,%15}, [%16];"
@@ -322,15 +351,19 @@ __global__ void __launch_bounds__(kVisThreads, 1)
             "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int jb = pass * kVisNP + ehalf * 256 + cb;
+      const int jb = jcol0 + cb;
+      // v-phase 2 v Y_jb (mod 2) in FP64, then rotations over the 16 columns
+      const double tvp = 2.0 * ev * (a.y_min + (jb + 0.5) * a.dy);
+      float sn, cs;
+      sincospif((float)(tvp - 2.0 * rint(0.5 * tvp)), &sn, &cs);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        if (jb + e >= a.ny) break;
-        float sn, cs;
-        sincospif(tv0 + (float)(cb + e) * dv, &sn, &cs);
-        const float D = __uint_as_float(r[e]);
+        const float D = (jb + e < a.ny) ? __uint_as_float(r[e]) : 0.f;
         accP = fmaf(cs, D, accP);
         accQ = fmaf(sn, D, accQ);
+        const float cn = fmaf(cs, vrot_c, -sn * vrot_s);
+        sn = fmaf(sn, vrot_c, cs * vrot_s);
+        cs = cn;
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -365,7 +398,8 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kVisNP));
   }
 }
 
@@ -402,7 +436,7 @@ extern "C" {
 bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes) {
   if (!cam || !bytes || cam->nx < 1 || cam->ny < 1) return BH_ERR_INVALID_ARG;
   int64_t nxp = ((int64_t)cam->nx + kVisKC - 1) / kVisKC * kVisKC;
-  *bytes = a256(sizeof(int)) + a256((size_t)cam->ny * 3 * nxp * 2);
+  *bytes = a256(sizeof(int)) + a256((size_t)cam->ny * 2 * nxp * 2);
   return BH_OK;
 }
 
@@ -439,12 +473,12 @@ bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv
   char* ws = static_cast<char*>(workspace);
   a.status = reinterpret_cast<int*>(ws);
   uint16_t* Bp = reinterpret_cast<uint16_t*>(ws + a256(sizeof(int)));
-  // TMA map of B': [ny rows][3 nxp] 16-bit, box 64 x 256, 128-byte swizzle
+  // TMA map of B2: [ny rows][2 nxp] 16-bit, box 64 x 256, 128-byte swizzle
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  cuuint64_t dims[2] = {(cuuint64_t)3 * a.nxp, (cuuint64_t)a.ny};
-  cuuint64_t strides[1] = {(cuuint64_t)3 * a.nxp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kVisKC, 256u};
+  cuuint64_t dims[2] = {(cuuint64_t)2 * a.nxp, (cuuint64_t)a.ny};
+  cuuint64_t strides[1] = {(cuuint64_t)2 * a.nxp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kVisKC, (cuuint32_t)kVisNP};
   cuuint32_t estr[2] = {1u, 1u};
   CUresult r = enc(&map, a.fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                    2, Bp, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
