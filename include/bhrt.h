@@ -240,6 +240,14 @@ bh_status bh_plan_create(int32_t n, const bh_spacetime* st, const bh_camera* cam
 bh_status bh_plan_launch(bh_plan plan, int32_t use_graph, void* stream);
 /* Records CUDA events around each trace launch (disables graph replay). */
 bh_status bh_plan_set_timing(bh_plan plan, int32_t enable);
+/* Fixes the launch shape of a persistent trace kernel of the plan: which = 0
+ * the main kernel (FP64, or the FP32 bulk of the mixed path), 1 the FP64
+ * promoted pass; blocks >= 1, threads 64 or 128 (a multiple of 32),
+ * variant 0 or 1 (the kernel build, as in bh_tune_report).  A grid smaller
+ * than the GPU's resident capacity leaves room for other work, e.g. a second
+ * plan on another stream.  Any captured graph is discarded. */
+bh_status bh_plan_set_launch(bh_plan plan, int32_t which, int32_t blocks, int32_t threads,
+                             int32_t variant);
 /* Counters of the last launch (blocking copy on `stream`). */
 bh_status bh_plan_stats(bh_plan plan, void* stream, bh_run_stats* out);
 bh_status bh_plan_destroy(bh_plan plan);

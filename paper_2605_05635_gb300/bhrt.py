@@ -231,6 +231,7 @@ def lib():
                                      C.c_void_p, P(C.c_void_p)]
         L.bh_plan_launch.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
         L.bh_plan_set_timing.argtypes = [C.c_void_p, C.c_int32]
+        L.bh_plan_set_launch.argtypes = [C.c_void_p] + [C.c_int32] * 4
         L.bh_plan_stats.argtypes = [C.c_void_p, C.c_void_p, P(RunStats)]
         L.bh_plan_destroy.argtypes = [C.c_void_p]
         L.bh_plan_autotune.argtypes = [C.c_void_p, C.c_void_p, P(TuneReport)]
@@ -255,7 +256,8 @@ def lib():
             getattr(L, fn).restype = C.c_int
         for fn in ("bh_host_geometry", "bh_workspace_size", "bh_trace_image", "bh_trace_batch",
                    "bh_points_workspace_size", "bh_trace_points", "bh_workspace_status",
-                   "bh_plan_create", "bh_plan_launch", "bh_plan_set_timing", "bh_plan_stats",
+                   "bh_plan_create", "bh_plan_launch", "bh_plan_set_timing", "bh_plan_set_launch",
+                   "bh_plan_stats",
                    "bh_plan_destroy"):
             getattr(L, fn).restype = C.c_int
         _lib = L
@@ -432,6 +434,11 @@ class Plan:
 
     def set_timing(self, enable: bool):
         _check(lib().bh_plan_set_timing(self._h, int(enable)), "bh_plan_set_timing")
+
+    def set_launch(self, which: int, blocks: int, threads: int = 128, variant: int = 0):
+        """Fix the persistent grid of the main (0) or FP64-pass (1) trace kernel."""
+        _check(lib().bh_plan_set_launch(self._h, which, blocks, threads, variant),
+               "bh_plan_set_launch")
 
     def stats(self, stream=None) -> dict:
         st = RunStats()

@@ -731,6 +731,20 @@ bh_status bh_plan_set_timing(bh_plan p, int32_t enable) {
   return BH_OK;
 }
 
+bh_status bh_plan_set_launch(bh_plan p, int32_t which, int32_t blocks, int32_t threads,
+                             int32_t variant) {
+  if (!p || which < 0 || which > 1 || blocks < 1 || (threads != 64 && threads != 128) ||
+      variant < 0 || variant >= kKernelVariants)
+    return BH_ERR_INVALID_ARG;
+  LaunchShape& sh = which == 0 ? p->shape : p->shape64;
+  sh = LaunchShape{blocks, threads, variant};
+  if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  return BH_OK;
+}
+
 bh_status bh_plan_stats(bh_plan p, void* stream, bh_run_stats* out) {
   if (!p || !out) return BH_ERR_INVALID_ARG;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
