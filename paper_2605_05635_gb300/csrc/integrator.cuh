@@ -104,6 +104,8 @@ constexpr DPRolled<T> make_rolled(const Tab& t) {
 }
 
 static __constant__ DPRolled<double> kDPr = make_rolled<double>(kDP);
+// state components the right-hand side reads: R, theta, p_R, p_theta
+__host__ __device__ constexpr int kQC(int x) { return x < 2 ? x + 1 : x + 2; }
 static __constant__ DPRolled<float> kDPrf = make_rolled<float>(kDPf);
 
 constexpr double kHalfPi = 1.57079632679489661923;
@@ -408,14 +410,18 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   // rolled stage loop (see DPRolled): k is the latest stage derivative, q[u]
   // the running input sums of the next stages, s5/se/sd the running sums of
   // the update, the error estimate and the dense-output term; r.f keeps k_0
-  double k[6], q[6][6], s5[6], se[6], sd[6];
+  // the right-hand side reads R, theta, p_R, p_theta only (T and phi are
+  // cyclic), so the stage-input sums q keep those four components (kQC)
+  double k[6], q[6][4], s5[6], se[6], sd[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     k[i] = r.f[i];
     s5[i] = se[i] = sd[i] = 0.0;
-#pragma unroll
-    for (int u = 0; u < 6; ++u) q[u][i] = 0.0;
   }
+#pragma unroll
+  for (int u = 0; u < 6; ++u)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) q[u][x] = 0.0;
   bool bad = false;
   double W = 0, P2oD = 1;
 #pragma unroll 1
@@ -444,21 +450,21 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
       if ((qm >> u) & 1) {
         const double c = kDPr.q[j][u];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) q[u][i] = fma(c, k[i], q[u][i]);
+        for (int x = 0; x < 4; ++x) q[u][x] = fma(c, k[kQC(x)], q[u][x]);
       }
     }
-    double ys[6];
+    double ys[4];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) ys[i] = r.y[i] + h * q[0][i];
-    bool ok = geo_rhs(m, r.E, r.ell, ys[1], ys[2], ys[4], ys[5], k, W, P2oD);
+    for (int x = 0; x < 4; ++x) ys[x] = r.y[kQC(x)] + h * q[0][x];
+    bool ok = geo_rhs(m, r.E, r.ell, ys[0], ys[1], ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) q[u][i] = q[u + 1][i];
+      for (int x = 0; x < 4; ++x) q[u][x] = q[u + 1][x];
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) q[5][i] = 0.0;
+    for (int x = 0; x < 4; ++x) q[5][x] = 0.0;
   }
   double y1[6];
   float err2 = 0.f;

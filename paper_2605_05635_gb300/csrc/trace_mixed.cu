@@ -309,14 +309,18 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   // k: the latest stage derivative; q[u]: running input sums of the next
   // stages; s5, se, sd: running sums of the update, the error estimate and
   // the dense-output term (see DPRolled).  r.f keeps k_0 until the end.
-  float k[6], q[6][6], s5[6], se[6], sd[6];
+  // stage-input sums only for R, theta, p_R, p_theta (kQC): T and phi are
+  // cyclic and never enter the right-hand side
+  float k[6], q[6][4], s5[6], se[6], sd[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     k[i] = r.f[i];
     s5[i] = se[i] = sd[i] = 0.f;
-#pragma unroll
-    for (int u = 0; u < 6; ++u) q[u][i] = 0.f;
   }
+#pragma unroll
+  for (int u = 0; u < 6; ++u)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) q[u][x] = 0.f;
   bool bad = false;
   float W = 0.f, P2oD = 1.f;
 #pragma unroll 1
@@ -336,20 +340,20 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     for (int u = 0; u < 6; ++u) {
       const float c = kDPrf.q[j][u];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) q[u][i] = fmaf(c, k[i], q[u][i]);
+      for (int x = 0; x < 4; ++x) q[u][x] = fmaf(c, k[kQC(x)], q[u][x]);
     }
-    float ys[6];
+    float ys[4];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) ys[i] = r.yh[i] + (r.yl[i] + h * q[0][i]);
-    bool ok = geo_rhs(mf, r.Ef, r.ellf, ys[1], ys[2], ys[4], ys[5], k, W, P2oD);
+    for (int x = 0; x < 4; ++x) ys[x] = r.yh[kQC(x)] + (r.yl[kQC(x)] + h * q[0][x]);
+    bool ok = geo_rhs(mf, r.Ef, r.ellf, ys[0], ys[1], ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) q[u][i] = q[u + 1][i];
+      for (int x = 0; x < 4; ++x) q[u][x] = q[u + 1][x];
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) q[5][i] = 0.f;
+    for (int x = 0; x < 4; ++x) q[5][x] = 0.f;
   }
   float dlt[6], err2 = 0.f;
 #pragma unroll

@@ -79,6 +79,7 @@ def test_argument_errors_return_before_device_work(B):
         code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(em), C.byref(badint), 0,
                                    None, None, ws, 0, None)
         assert code == 1
+    assert lib.bh_plan_set_launch(None, 0, 1, 128, 0) == 1   # no plan
     incl = B.Camera(incl=math.pi)._c()
     code = lib.bh_trace_points(C.byref(st), C.byref(incl), C.byref(em), C.byref(it), 0, None,
                                None, ws, 0, None)
