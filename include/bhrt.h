@@ -142,6 +142,11 @@ typedef struct {
   int64_t refine_keys_cap;   /* capacity of refine_keys                      */
   int64_t* refine_keys_count; /* optional device int64: number of keys (may
                                  exceed the capacity, then the list is cut) */
+  int32_t* steps;         /* optional [2][ny*nx]: accepted and rejected
+                             Dormand-Prince steps of the base ray (all
+                             precisions together)                          */
+  uint8_t* promoted;      /* optional [ny*nx]: 1 if the base ray took FP64
+                             steps on the mixed path, else 0               */
 } bh_image_out;
 
 /* Per-ray record returned by bh_trace_points (device array of structs). */

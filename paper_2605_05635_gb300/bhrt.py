@@ -67,7 +67,8 @@ class _ImageOut(C.Structure):
                 ("status", C.c_void_p), ("refine_level", C.c_void_p), ("R_em", C.c_void_p),
                 ("phi_em", C.c_void_p), ("T_em", C.c_void_p), ("g", C.c_void_p),
                 ("h_drift", C.c_void_p), ("refine_keys", C.c_void_p),
-                ("refine_keys_cap", C.c_int64), ("refine_keys_count", C.c_void_p)]
+                ("refine_keys_cap", C.c_int64), ("refine_keys_count", C.c_void_p),
+                ("steps", C.c_void_p), ("promoted", C.c_void_p)]
 
 
 class RayRecord(C.Structure):
@@ -314,7 +315,9 @@ def alloc_outputs(cam: Camera, device, keys_cap: int = 0) -> Dict[str, torch.Ten
                ncross=torch.empty(ny, nx, **u8), status=torch.empty(ny, nx, **u8),
                refine_level=torch.empty(ny, nx, **u8), R_em=torch.empty(3, ny, nx, **f),
                phi_em=torch.empty(3, ny, nx, **f), T_em=torch.empty(3, ny, nx, **f),
-               g=torch.empty(3, ny, nx, **f), h_drift=torch.empty(ny, nx, **f))
+               g=torch.empty(3, ny, nx, **f), h_drift=torch.empty(ny, nx, **f),
+               steps=torch.empty(2, ny, nx, dtype=torch.int32, device=device),
+               promoted=torch.empty(ny, nx, **u8))
     if keys_cap:
         out["refine_keys"] = torch.empty(keys_cap, dtype=torch.int64, device=device)
         out["refine_keys_count"] = torch.zeros(1, dtype=torch.int64, device=device)
@@ -330,7 +333,7 @@ def _image_out(o: Dict[str, torch.Tensor]) -> _ImageOut:
     return _ImageOut(ptr("I"), ptr("I_n"), ptr("ncross"), ptr("status"), ptr("refine_level"),
                      ptr("R_em"), ptr("phi_em"), ptr("T_em"), ptr("g"), ptr("h_drift"),
                      ptr("refine_keys"), keys.numel() if keys is not None else 0,
-                     ptr("refine_keys_count"))
+                     ptr("refine_keys_count"), ptr("steps"), ptr("promoted"))
 
 
 def trace_batch(items: Sequence[tuple], device=None, stream=None, keys_cap: int = 0,

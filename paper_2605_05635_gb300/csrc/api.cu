@@ -2,8 +2,10 @@
 // extremal spin, ISCO, ZAMO frame), workspace layout and the launch
 // sequence of one tracing call.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -412,6 +414,8 @@ bh_status plan_build(int32_t n, const bh_spacetime* st, const bh_camera* cam,
     d.keys = o.refine_keys;
     d.keys_cap = o.refine_keys ? o.refine_keys_cap : 0;
     d.keys_count = reinterpret_cast<unsigned long long*>(o.refine_keys_count);
+    d.steps = o.steps;
+    d.promoted = o.promoted;
     if (d.keys_count) p.any_keys = true;
     if (integ[i].time_budget_s > budget) budget = integ[i].time_budget_s;
   }
@@ -494,6 +498,10 @@ bh_status enqueue(const bh_plan_s& p, cudaStream_t s) {
     if (o.g && cudaMemsetAsync(o.g, 0, plane, s) != cudaSuccess) return BH_ERR_CUDA;
     if (o.keys_count && cudaMemsetAsync(o.keys_count, 0, sizeof(unsigned long long), s) != cudaSuccess)
       return BH_ERR_CUDA;
+    if (o.steps && cudaMemsetAsync(o.steps, 0, sizeof(int32_t) * 2 * p.npix, s) != cudaSuccess)
+      return BH_ERR_CUDA;
+    if (o.promoted && cudaMemsetAsync(o.promoted, 0, p.npix, s) != cudaSuccess)
+      return BH_ERR_CUDA;
   }
   WsHeader* hdr = reinterpret_cast<WsHeader*>(p.ws + p.L.hdr);
   if (launch_begin(hdr, p.budget_ns, s) != cudaSuccess) return BH_ERR_CUDA;
@@ -529,8 +537,15 @@ bh_status enqueue(const bh_plan_s& p, cudaStream_t s) {
       }
       const cudaEvent_t* ev = &p.ev[2 * (3 * level + pass)];
       if (p.timing && cudaEventRecord(ev[0], s) != cudaSuccess) return cudaErrorUnknown;
+      // host-side profiler range per level and pass (no cost without a tool)
+      static const char* kPassName[3] = {"main", "fp64 promoted", "fp32 demoted"};
+      char label[64];
+      std::snprintf(label, sizeof(label), "bhrt trace level %d %s", level,
+                    p.precision == 0 ? "fp64" : kPassName[pass]);
+      nvtxRangePushA(label);
       cudaError_t e = (p.precision == 0 || pass == 1) ? launch_trace_fp64(b, p.shape64, s)
                                                       : launch_trace_mixed(b, p.shape, s);
+      nvtxRangePop();
       if (e == cudaSuccess && p.timing) e = cudaEventRecord(ev[1], s);
       if (e != cudaSuccess) return e;
     }
@@ -538,7 +553,10 @@ bh_status enqueue(const bh_plan_s& p, cudaStream_t s) {
   };
   if (trace(0) != cudaSuccess) return BH_ERR_CUDA;
   for (int l = 0; l < p.levels; ++l) {
-    if (launch_mark_expand(ra, l, p.refine_blocks, s) != cudaSuccess) return BH_ERR_CUDA;
+    nvtxRangePushA("bhrt refine mark and expand");
+    cudaError_t e = launch_mark_expand(ra, l, p.refine_blocks, s);
+    nvtxRangePop();
+    if (e != cudaSuccess) return BH_ERR_CUDA;
     if (trace(l + 1) != cudaSuccess) return BH_ERR_CUDA;
   }
   for (int l = p.levels > 0 ? p.levels - 1 : 0; l >= 0; --l)

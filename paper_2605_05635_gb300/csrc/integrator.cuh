@@ -639,6 +639,13 @@ __device__ __forceinline__ void finish_ray(const TraceArgs& a, int64_t item, uin
     o.status[pix] = (uint8_t)status;
     o.ncross[pix] = (uint8_t)nc;
     if (o.h_drift) o.h_drift[pix] = hdrift;
+    if (o.steps) {
+      o.steps[pix] = nacc;
+      o.steps[a.npix + pix] = nrej;
+    }
+    // a ray finishing in a resumed pass (FP64 promoted, or FP32 after
+    // demotion) took FP64 steps
+    if (o.promoted) o.promoted[pix] = (uint8_t)(a.source == 1);
   } else {
     int64_t c = a.lv.cap;
     a.lv.I[item] = cs.I[0];

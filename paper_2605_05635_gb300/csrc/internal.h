@@ -26,6 +26,8 @@ struct OutPtrs {
   uint64_t* keys;
   int64_t keys_cap;
   unsigned long long* keys_count;
+  int32_t* steps;       // optional [2][npix] accepted, rejected steps of the base ray
+  uint8_t* promoted;    // optional [npix] base ray took FP64 steps (mixed path)
 };
 
 // Everything a trace launch needs (passed by value as a kernel parameter).

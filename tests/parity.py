@@ -28,6 +28,23 @@ def oracle_class_is_undetermined(oracle, flat: dict, X: float, Y: float) -> bool
     return bool(a["near_thdot"] < 1e-9 or a["near_dlam"] < 1e-9)
 
 
+def class_sensitive(oracle, flat: dict, X: float, Y: float, eps: float = 1e-6) -> bool:
+    """Exemption rule of the mixed-precision path: the oracle's own class at
+    (X, Y) changes under a relative screen perturbation of eps, or among the
+    tolerance pairs (rtol, atol) = (1e-8, 1e-8), (1e-8, 1e-10), (1e-10,
+    1e-12), (1e-12, 1e-14)."""
+    base = oracle_flat(flat, oracle)
+    pts = [[X, Y]]
+    d = eps * max(abs(X), abs(Y), 1.0)
+    pts += [[X + d, Y], [X - d, Y], [X, Y + d], [X, Y - d]]
+    classes = set()
+    for rtol, atol in ((1e-8, 1e-8), (1e-8, 1e-10), (1e-10, 1e-12), (1e-12, 1e-14)):
+        P = oracle.problem(**{**base, "rtol": rtol, "atol": atol})
+        for r in oracle.trace_points(P, pts):
+            classes.add((int(r["status"]), int(r["ncross"])))
+    return len(classes) > 1
+
+
 def oracle_flat(flat: dict, oracle) -> dict:
     return {k: v for k, v in flat.items() if k in oracle.DEFAULTS}
 

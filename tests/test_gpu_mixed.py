@@ -12,7 +12,7 @@ import math
 import numpy as np
 import pytest
 
-from parity import oracle_flat, pixel_centre
+from parity import class_sensitive, oracle_flat, pixel_centre
 
 pytestmark = pytest.mark.gpu
 
@@ -27,19 +27,6 @@ def B():
     import paper_2605_05635_gb300 as B
     B.lib()
     return B
-
-
-def class_sensitive(oracle, flat, X, Y, eps=1e-6):
-    base = oracle_flat(flat, oracle)
-    pts = [[X, Y]]
-    d = eps * max(abs(X), abs(Y), 1.0)
-    pts += [[X + d, Y], [X - d, Y], [X, Y + d], [X, Y - d]]
-    classes = set()
-    for rtol, atol in ((1e-8, 1e-8), (1e-8, 1e-10), (1e-10, 1e-12), (1e-12, 1e-14)):
-        P = oracle.problem(**{**base, "rtol": rtol, "atol": atol})
-        for r in oracle.trace_points(P, pts):
-            classes.add((int(r["status"]), int(r["ncross"])))
-    return len(classes) > 1
 
 
 def _mixed_flat(workloads, **kw):

@@ -118,3 +118,25 @@ def test_visibilities_large_image_vs_gpu_fp64(B):
     Vt = B.visibilities(It, cam, uv, mode=1).cpu().numpy()
     Vd = B.visibilities_fp64(It, cam, uv).cpu().numpy()
     assert np.max(np.abs(Vt - Vd)) / abs(Vd[0]) <= 2e-4
+
+
+def test_visibilities_widest_screen_and_ragged_baselines(B):
+    """nx = 4096, the widest screen the tensor-core path takes (its per-CTA
+    phase table), a short screen (40 rows of one 256-row pass) and 70
+    baselines (a ragged last CTA), against the FP64 direct mode; nx = 4097
+    is refused before any work."""
+    import torch
+    from paper_2605_05635_gb300 import workloads
+    nx, ny = 4096, 40
+    rng = np.random.default_rng(11)
+    I = rng.random((ny, nx)).astype(np.float32)
+    cam = B.Camera(nx=nx, ny=ny, x_min=-12.0, x_max=12.0, y_min=-1.0, y_max=1.0)
+    uv = torch.from_numpy(np.concatenate([[[0.0, 0.0]], workloads.uv_points(69, seed=7)]))
+    It = torch.from_numpy(I).cuda()
+    Vt = B.visibilities(It, cam, uv, mode=1).cpu().numpy()
+    Vd = B.visibilities_fp64(It, cam, uv).cpu().numpy()
+    assert Vt.shape == (70,)
+    assert np.max(np.abs(Vt - Vd)) / abs(Vd[0]) <= 2e-4
+    wide = B.Camera(nx=nx + 1, ny=ny, x_min=-12.0, x_max=12.0, y_min=-1.0, y_max=1.0)
+    with pytest.raises(B.BHRTError):
+        B.visibilities(torch.zeros(ny, nx + 1, device="cuda"), wide, uv, mode=1)

@@ -195,3 +195,27 @@ def test_queue_overflow_returns_status(B):
     with pytest.raises(B.BHRTError) as e:
         B.trace_image(st, cam, em, it)
     assert e.value.code == 7
+
+
+def test_step_and_promotion_planes(B):
+    """Per-pixel step counters equal those of the same rays traced as points
+    (the same step sequence); the FP64 path promotes nothing; on the mixed
+    path every captured base ray took FP64 steps (promotion within 0.1 M of
+    the horizon comes before capture at 1.01 R_+)."""
+    from paper_2605_05635_gb300 import workloads
+    flat = workloads.kerr_64()
+    g = _gpu_image(B, flat)
+    st, cam, em, it = B.from_flat(flat)
+    xy = [pixel_centre(flat, i, j) for j in range(0, 64, 7) for i in range(0, 64, 5)]
+    rec = B.trace_points(st, cam, em, it, xy)
+    k = 0
+    for j in range(0, 64, 7):
+        for i in range(0, 64, 5):
+            assert g["steps"][0, j, i] == rec[k]["n_accept"]
+            assert g["steps"][1, j, i] == rec[k]["n_reject"]
+            k += 1
+    assert not g["promoted"].any() and (g["steps"][0] > 0).all()
+    mixed = _gpu_image(B, dict(flat, **workloads.MIXED_INTEG, chi=0.9))
+    captured = mixed["status"] == 1
+    assert captured.any() and (mixed["promoted"][captured] == 1).all()
+    assert (mixed["steps"][0] > 0).all()
