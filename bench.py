@@ -108,6 +108,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(rays: float, ms: float, world: int, device):
+    """Whole-job aggregation across ranks: the sum of the rays every rank
+    traced and the longest rank's timed duration (the job ends with it)."""
+    import torch
+    import torch.distributed as dist
+    tot = torch.tensor([float(rays), float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        r_sum = tot[0:1].clone()
+        t_max = tot[1:2].clone()
+        dist.all_reduce(r_sum, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        tot = torch.cat([r_sum, t_max])
+    return float(tot[0]), float(tot[1])
+
+
 def cpu_baseline(flats, seconds: float, seed: int = 7):
     """The oracle (plain FP64 C, OpenMP over pixels) on a bounded random sample
     of base pixels of the same images, each with its refinement subtree."""
@@ -620,15 +635,7 @@ def main():
         ms = t0.elapsed_time(t1)
     plan.set_timing(False)
 
-    # whole-job aggregation (max time over ranks, sum of rays)
-    tot = torch.tensor([float(rays), ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        r_sum = tot[0:1].clone()
-        t_max = tot[1:2].clone()
-        dist.all_reduce(r_sum, op=dist.ReduceOp.SUM)
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        tot = torch.cat([r_sum, t_max])
-    all_rays, max_ms = float(tot[0]), float(tot[1])
+    all_rays, max_ms = aggregate_ranks(rays, ms, world, dev)
     value = all_rays / (max_ms / 1e3)
     images_per_s = world * len(items) * args.steps / (max_ms / 1e3)
 
