@@ -498,6 +498,49 @@ def run_adjoint(args, B, workloads, dev, stream):
     print(json.dumps(line), flush=True)
 
 
+METRIC_C1 = "geodesic rays/s, Kerr 64^2 parity case (FP64), with the oracle's time for the image"
+WORKLOAD_C1 = ("Kerr a=0.5 incl 17 deg, R_o=1000, 64x64 cell-centred over [-10,10]^2, no "
+               "refinement, FP64 rtol 1e-10 (the oracle-sized parity case)")
+
+
+def run_kerr64(args, B, workloads, dev, stream):
+    """The small parity case: one 64^2 Kerr image in FP64, timed on the GPU,
+    and the whole image by the oracle on the host cores."""
+    import torch
+
+    import oracle
+    flat = workloads.kerr_64()
+    items = [B.from_flat(flat)]
+    plan = B.Plan(items, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.launch(stream=stream)
+        plan.check(stream)
+        ms = _events_ms(stream, lambda: plan.launch(stream=stream), args.steps)
+        st = plan.stats(stream)
+    rays = sum(st["rays"])
+    plan.close()
+    oracle.build()
+    P = oracle.problem(**{k: v for k, v in flat.items() if k in oracle.DEFAULTS})
+    t0 = time.perf_counter()
+    oracle.trace_image(P)
+    t_or = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "metric": METRIC_C1, "value": rays / (ms / 1e3), "unit": "rays/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_C1, "nx": 64, "ny": 64,
+                                        "parallelism": "dp1"},
+        "note": "4096 rays fill 3 % of the GPU's resident threads: a latency figure, not a "
+                "throughput one",
+        "cpu_baseline": {"value": rays / t_or, "unit": "rays/s", "cores": cores,
+                         "kind": "oracle", "sample": f"the whole image, {t_or:.2f} s"},
+        "oracle_seconds_for_image": t_or,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _measured_peak(key):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -544,7 +587,7 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
-    ap.add_argument("--workload", choices=["sweep512", "sweep96", "vis1024", "adjoint256"],
+    ap.add_argument("--workload", choices=["sweep512", "sweep96", "vis1024", "adjoint256", "kerr64"],
                     default="sweep512",
                     help="sweep512: the headline line; sweep96 and vis1024: the batched-sweep "
                          "and visibility measurements")
@@ -563,7 +606,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2605_05635_gb300 as B
-    from paper_2605_05635_gb300 import bhrt, workloads
+    from paper_2605_05635_gb300 import workloads
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -579,24 +622,16 @@ def main():
         B.lib()
     except Exception as e:  # the CUDA library is the product; no fallback
         raise SystemExit(f"libbhrt unavailable: {e}")
-    try:
-        bhrt.Integrator(precision=prec)
-        flats = workloads.sweep_512(precision=prec)
-        items = [B.from_flat(d) for d in flats]
-        plan = B.Plan(items, device=dev, keys_cap=KEYS_CAP)
-    except B.BHRTError:
-        prec = B.FP64
-        flats = workloads.sweep_512(precision=prec)
-        items = [B.from_flat(d) for d in flats]
-        plan = B.Plan(items, device=dev, keys_cap=KEYS_CAP)
     stream = torch.cuda.Stream(device=dev)
     if args.workload != "sweep512":
         if world > 1:
-            raise SystemExit("--workload sweep96/vis1024 run on one GPU")
-        plan.close()
+            raise SystemExit(f"--workload {args.workload} runs on one GPU")
         fn = {"sweep96": run_sweep96, "vis1024": run_vis1024,
-              "adjoint256": run_adjoint}[args.workload]
+              "adjoint256": run_adjoint, "kerr64": run_kerr64}[args.workload]
         return fn(args, B, workloads, dev, stream)
+    flats = workloads.sweep_512(precision=prec)
+    items = [B.from_flat(d) for d in flats]
+    plan = B.Plan(items, device=dev, keys_cap=KEYS_CAP)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
