@@ -33,7 +33,7 @@ struct alignas(16) ImgParams {
   double j0, p, R_s, sig_in, sig_out, R_out;
   double rtol, atol, thdot_min, dlam_min, promote_R, demote_R;
   int32_t promote_ncross;  // mixed: promote once N_cross reaches this inside demote_R
-  int32_t pad1;
+  float pi_beta;           // mixed FP32 steps: PI step-size controller beta (0: plain)
 };
 
 // Workspace header (first 256 bytes of every workspace).
@@ -112,8 +112,9 @@ __device__ __forceinline__ float d_log1p(float x) {
 // FP64 sine and cosine without a slow path, for the polar angle and trial
 // stages a few radians around it: Cody & Waite reduction by the nearest
 // multiple q of pi/2 with a two-part constant (exact to far below one unit
-// for |q| < 2^20), Taylor polynomials of sin r to r^19 and cos r to r^18 on
-// |r| <= pi/4 (truncation below 2e-21), then a rotation by q quarter turns;
+// for |q| < 2^20), Taylor polynomials of sin r to r^17 and cos r to r^16 on
+// |r| <= pi/4 (truncation below 2e-18 relative), then a rotation by q
+// quarter turns;
 // q is rounded by adding 1.5 * 2^52, whose low mantissa bits hold q mod 4.
 __device__ __forceinline__ void d_sincos(double x, double* s, double* c) {
   const double qm = fma(x, 0.63661977236758134308, 6755399441055744.0);
@@ -122,8 +123,7 @@ __device__ __forceinline__ void d_sincos(double x, double* s, double* c) {
   double r = fma(q, -1.5707963267948966192, x);            // pi/2, leading part
   r = fma(q, -6.1232339957367660359e-17, r);               // pi/2, trailing part
   const double r2 = r * r;
-  double ps = fma(r2, -8.22063524662433e-18, 2.8114572543455206e-15);  // -1/19!, 1/17!
-  ps = fma(ps, r2, -7.647163731819816e-13);  // -1/15!
+  double ps = fma(r2, 2.8114572543455206e-15, -7.647163731819816e-13);  // 1/17!, -1/15!
   ps = fma(ps, r2, 1.6059043836821613e-10);  // 1/13!
   ps = fma(ps, r2, -2.505210838544172e-08);  // -1/11!
   ps = fma(ps, r2, 2.7557319223985893e-06);  // 1/9!
@@ -131,8 +131,7 @@ __device__ __forceinline__ void d_sincos(double x, double* s, double* c) {
   ps = fma(ps, r2, 0.008333333333333333);  // 1/5!
   ps = fma(ps, r2, -0.16666666666666666);  // -1/3!
   const double sr = fma(ps * r2, r, r);
-  double pc = fma(r2, -1.5619206968586225e-16, 4.779477332387385e-14);  // -1/18!, 1/16!
-  pc = fma(pc, r2, -1.1470745597729725e-11);  // -1/14!
+  double pc = fma(r2, 4.779477332387385e-14, -1.1470745597729725e-11);  // 1/16!, -1/14!
   pc = fma(pc, r2, 2.08767569878681e-09);  // 1/12!
   pc = fma(pc, r2, -2.755731922398589e-07);  // -1/10!
   pc = fma(pc, r2, 2.48015873015873e-05);  // 1/8!
