@@ -121,12 +121,6 @@ typedef struct {
                            FP64 steps until outgoing beyond R = 10;
                            0..1000, 1000 = never                          */
   int32_t reserved;     /* must be 0                                        */
-  double pi_beta;       /* mixed, FP32 steps: 0 for the plain step-size
-                           controller, else the beta of a PI controller
-                           h *= 0.9 err^-(0.2 - 0.75 beta) err_prev^beta
-                           (Gustafsson; Hairer-Norsett-Wanner II.4), which
-                           damps the step-size oscillation FP32 round-off
-                           in the error estimate excites; 0 .. 0.2          */
 } bh_integrator;
 
 /* Per-pixel output planes (device pointers, caller-owned).  Any pointer

@@ -59,8 +59,7 @@ class _Integrator(C.Structure):
                 ("atol", C.c_double), ("cap_factor", C.c_double), ("esc_factor", C.c_double),
                 ("thetadot_min", C.c_double), ("dlambda_min", C.c_double),
                 ("promote_dr", C.c_double), ("time_budget_s", C.c_double),
-                ("promote_order", C.c_int32), ("reserved", C.c_int32),
-                ("pi_beta", C.c_double)]
+                ("promote_order", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _ImageOut(C.Structure):
@@ -169,13 +168,12 @@ class Integrator:
     promote_dr: float = 0.1
     time_budget_s: float = 0.0
     promote_order: int = 2
-    pi_beta: float = 0.0
 
     def _c(self):
         return _Integrator(self.precision, self.max_steps, self.rtol, self.atol,
                            self.cap_factor, self.esc_factor, self.thetadot_min,
                            self.dlambda_min, self.promote_dr, self.time_budget_s,
-                           self.promote_order, 0, self.pi_beta)
+                           self.promote_order, 0)
 
 
 def from_flat(d: dict):
@@ -199,8 +197,7 @@ def from_flat(d: dict):
                     dlambda_min=d.get("dlambda_min", 1e-6),
                     promote_dr=d.get("promote_dr", 0.1),
                     time_budget_s=d.get("time_budget_s", 0.0),
-                    promote_order=d.get("promote_order", 2),
-                    pi_beta=d.get("pi_beta", 0.0))
+                    promote_order=d.get("promote_order", 2))
     return st, cam, em, it
 
 

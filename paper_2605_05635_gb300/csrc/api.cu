@@ -188,7 +188,7 @@ bh_status validate(const bh_spacetime& s, const bh_camera& c, const bh_emission&
   if (!finite_pos(g.rtol) || !finite_pos(g.atol) || !(g.cap_factor >= 1.0) ||
       !(g.esc_factor > 1.0) || !(g.thetadot_min >= 0.0) || !(g.dlambda_min >= 0.0) ||
       !(g.promote_dr >= 0.0) || !(g.time_budget_s >= 0.0) || g.promote_order < 0 ||
-      g.promote_order > 1000 || g.reserved != 0 || !(g.pi_beta >= 0.0 && g.pi_beta <= 0.2))
+      g.promote_order > 1000 || g.reserved != 0)
     return BH_ERR_INVALID_ARG;
   return BH_OK;
 }
@@ -256,7 +256,6 @@ bh_status make_params(const bh_spacetime& s, const bh_camera& c, const bh_emissi
   ip.promote_R = rp + g.promote_dr;
   ip.demote_R = kDemoteR;
   ip.promote_ncross = g.promote_order + 1;
-  ip.pi_beta = (float)g.pi_beta;
   return BH_OK;
 }
 

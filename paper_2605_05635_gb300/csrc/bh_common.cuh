@@ -33,7 +33,7 @@ struct alignas(16) ImgParams {
   double j0, p, R_s, sig_in, sig_out, R_out;
   double rtol, atol, thdot_min, dlam_min, promote_R, demote_R;
   int32_t promote_ncross;  // mixed: promote once N_cross reaches this inside demote_R
-  float pi_beta;           // mixed FP32 steps: PI step-size controller beta (0: plain)
+  int32_t pad1;
 };
 
 // Workspace header (first 256 bytes of every workspace).

@@ -72,7 +72,6 @@ struct RayMx {
   float Ef, ellf;
   CrossState cs;
   float hdrift;
-  float errold;        // error norm of the last accepted step (PI controller)
   int32_t nacc, nrej, steps;
   bool rejected;
 };
@@ -95,7 +94,6 @@ __device__ __forceinline__ void mx_from64(const Ray64& r, RayMx& x) {
   x.nrej = r.nrej;
   x.steps = r.steps;
   x.rejected = r.rejected;
-  x.errold = 1e-4f;
 }
 
 __device__ __forceinline__ void mx_spill(const RayMx& x, int64_t item, uint32_t img,
@@ -136,7 +134,6 @@ __device__ __forceinline__ void mx_resume(const SpillRec& s, const MetricConsts<
   x.cs.ncross = s.ncross;
   x.cs.have_trusted = (s.flags & 1) != 0;
   x.rejected = (s.flags & 2) != 0;
-  x.errold = 1e-4f;
   x.hdrift = s.hdrift;
   x.nacc = s.nacc;
   x.nrej = s.nrej;
@@ -147,7 +144,6 @@ __device__ __forceinline__ void mx_resume(const SpillRec& s, const MetricConsts<
 struct MxConsts {
   float rtol, atol, R_cap, R_esc, promote_R, demote_R;
   int promote_nc;
-  float pi_beta;
 };
 
 // Launch of the mixed path: the constants of motion and the launch momenta
@@ -196,7 +192,6 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   r.cs.ncross = 0;
   r.cs.I[0] = r.cs.I[1] = r.cs.I[2] = r.cs.I[3] = 0.0;
   r.rejected = false;
-  r.errold = 1e-4f;
   r.nacc = r.nrej = r.steps = 0;
   r.hdrift = 0.f;
 }
@@ -430,18 +425,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   const float R = r.yh[1];
   if (R < c.R_cap) return 2;
   if (R > c.R_esc) return 1;
-  // plain controller, or the PI controller (Gustafsson 1991, in the form of
-  // Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4) when beta > 0
-  const float beta = c.pi_beta;
-  if (beta > 0.f) {
-    float fac = (err == 0.f) ? 10.f
-                             : 0.9f * __powf(err, 0.75f * beta - 0.2f) * __powf(r.errold, beta);
-    fac = fminf(fmaxf(fac, 0.2f), r.rejected ? 1.f : 10.f);
-    r.h = h * fac;
-    r.errold = fmaxf(err, 1e-4f);
-  } else {
-    r.h = h * step_factor(err, r.rejected);
-  }
+  r.h = h * step_factor(err, r.rejected);
   r.rejected = false;
   // image order n = N_cross - 1 (Sec. 4.2): rays winding to n >= promote_order
   // are promoted
@@ -504,7 +488,6 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
         c.promote_R = (float)ip->promote_R;
         c.demote_R = (float)ip->demote_R;
         c.promote_nc = ip->promote_ncross;
-        c.pi_beta = ip->pi_beta;
         active = true;
       } else {
         drained = true;
