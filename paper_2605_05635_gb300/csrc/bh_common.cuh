@@ -185,6 +185,18 @@ __device__ __forceinline__ double d_rcp(double x) {
   return fma(r, e, r);
 }
 __device__ __forceinline__ float d_rcp(float x) { return __fdividef(1.0f, x); }
+
+// FP64 1/sqrt(x) for normal, finite x > 0 without a slow path: the
+// hardware's approximate reciprocal square root (rsqrt.approx.ftz.f64)
+// refined by two Newton steps y <- y (3 - x y^2) / 2, within about one unit
+// in the last place.
+__device__ __forceinline__ double d_rsqrt(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double hx = 0.5 * x;
+  y = y * fma(-hx, y * y, 1.5);
+  return y * fma(-hx, y * y, 1.5);
+}
 // FP64 exp without a slow path: x = k ln2 + r with k the nearest integer to
 // x / ln2 (rounded by adding 1.5 * 2^52) and r reduced by a two-part ln 2
 // (Cody & Waite), |r| <= ln2 / 2; e^r by its Taylor series to r^13

@@ -116,7 +116,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // Step-size factor: safety 0.9, clamp [0.2, 10], no growth right after a
 // rejection; err^(-1/5) evaluated in FP32 (it only steers the step size).
 __device__ __forceinline__ float step_factor(float e, bool after_reject) {
-  float fac = (e == 0.f) ? 10.f : 0.9f * exp2f(-0.2f * log2f(e));
+  float fac = (e == 0.f) ? 10.f : 0.9f * __powf(e, -0.2f);
   return fminf(fmaxf(fac, 0.2f), after_reject ? 1.f : 10.f);
 }
 
@@ -301,8 +301,7 @@ struct Ray64 {
 // Sec. II.4) for an error estimator of order 4.  All in FP64.
 __device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricConsts<double>& m,
                                            double X, double Y, Ray64& r) {
-  double d = sqrt(ip.r_obs * ip.r_obs + X * X + Y * Y);
-  double id = 1.0 / d;
+  const double id = d_rsqrt(ip.r_obs * ip.r_obs + X * X + Y * Y);
   r.y[0] = 0.0;
   r.y[1] = ip.r_obs;
   r.y[2] = ip.incl;
@@ -336,7 +335,7 @@ __device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricCons
   }
   d2 = __fdividef(sqrtf(d2 / 6.f), h0);
   const float mx = fmaxf(d1, d2);
-  const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : exp2f(0.2f * log2f(0.01f / mx));
+  const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : __powf(__fdividef(0.01f, mx), 0.2f);
   r.h = (double)fminf(100.f * h0, h1);
   r.lam = 0.0;
   r.cs.lam_last = 0.0;

@@ -151,7 +151,7 @@ struct MxConsts {
 // Hairer-Wanner starting step in FP32.
 __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricConsts<float>& mf,
                                             const MxConsts& c, double X, double Y, RayMx& r) {
-  const double d = sqrt(ip.r_obs * ip.r_obs + X * X + Y * Y), id = 1.0 / d;
+  const double id = d_rsqrt(ip.r_obs * ip.r_obs + X * X + Y * Y);
   r.ell = ip.sq_gph * (-X * id);
   r.E = ip.zamo_N + ip.zamo_w * r.ell;
   df_from(0.0, r.yh[0], r.yl[0]);
@@ -167,24 +167,25 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     sc[i] = c.atol + c.rtol * fabsf(r.yh[i]);
-    d0 += (r.yh[i] / sc[i]) * (r.yh[i] / sc[i]);
-    d1 += (r.f[i] / sc[i]) * (r.f[i] / sc[i]);
+    const float a0 = __fdividef(r.yh[i], sc[i]), a1 = __fdividef(r.f[i], sc[i]);
+    d0 += a0 * a0;
+    d1 += a1 * a1;
   }
   d0 = sqrtf(d0 / 6.f);
   d1 = sqrtf(d1 / 6.f);
-  const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * d0 / d1;
+  const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * __fdividef(d0, d1);
   float f1[6];
   rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1] + h0 * r.f[1], r.yh[2] + h0 * r.f[2],
                r.yh[4] + h0 * r.f[4], r.yh[5] + h0 * r.f[5], f1);
   float d2 = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    const float q = (f1[i] - r.f[i]) / sc[i];
+    const float q = __fdividef(f1[i] - r.f[i], sc[i]);
     d2 += q * q;
   }
-  d2 = sqrtf(d2 / 6.f) / h0;
+  d2 = __fdividef(sqrtf(d2 / 6.f), h0);
   const float mx = fmaxf(d1, d2);
-  const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : exp2f(0.2f * log2f(0.01f / mx));
+  const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : __powf(__fdividef(0.01f, mx), 0.2f);
   r.h = fminf(100.f * h0, h1);
   r.lh = r.ll = 0.f;
   r.cs.lam_last = 0.0;

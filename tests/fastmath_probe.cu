@@ -1,4 +1,5 @@
-// Test probe: evaluates the sine/cosine, log(1 + x), exp and reciprocal of the
+// Test probe: evaluates the sine/cosine, log(1 + x), exp, reciprocal and
+// reciprocal square root of the
 // tracing kernels (bh_common.cuh) in FP32 and FP64 on given arguments, for
 // the accuracy tests in test_gpu_fastmath.py.  Test infrastructure, not part
 // of the library.
@@ -17,7 +18,7 @@ __global__ void probe_f32(int n, const float* x, float* s, float* c, float* l) {
 }
 
 __global__ void probe_f64(int n, const double* x, double* s, double* c, double* l, double* e,
-                          double* r) {
+                          double* r, double* q) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double a, b;
@@ -27,6 +28,7 @@ __global__ void probe_f64(int n, const double* x, double* s, double* c, double* 
   l[i] = bhrt::d_log1p(x[i]);
   e[i] = bhrt::d_exp(x[i]);
   r[i] = bhrt::d_rcp(x[i]);
+  q[i] = x[i] > 0.0 ? bhrt::d_rsqrt(x[i]) : 0.0;
 }
 
 extern "C" int fastmath_probe_f32(int n, const float* x, float* s, float* c, float* l) {
@@ -36,8 +38,8 @@ extern "C" int fastmath_probe_f32(int n, const float* x, float* s, float* c, flo
 }
 
 extern "C" int fastmath_probe_f64(int n, const double* x, double* s, double* c, double* l,
-                                  double* e, double* r) {
+                                  double* e, double* r, double* q) {
   if (n <= 0) return 0;
-  probe_f64<<<(n + 255) / 256, 256>>>(n, x, s, c, l, e, r);
+  probe_f64<<<(n + 255) / 256, 256>>>(n, x, s, c, l, e, r, q);
   return (int)cudaDeviceSynchronize();
 }

@@ -10,8 +10,8 @@ sine and cosine within 4u absolute over the polar angle and the trial
 stages around it, [-0.6, pi + 0.6], and the sine within 8u relative next to
 the poles (1/sin(theta) enters the right-hand side); log(1 + x) within 8u
 relative on [1e-3, 1e3] (x = R / lambda_c of the cored-NFW lapse); exp (FP64)
-within 8u relative on [-700, 5] and 0 below -708; the reciprocal (FP64)
-within 4u relative.
+within 8u relative on [-700, 5] and 0 below -708; the reciprocal and the
+reciprocal square root (FP64) within 4u relative.
 """
 import ctypes as C
 import math
@@ -44,7 +44,7 @@ def lib(tmp_path_factory):
     subprocess.run(cmd, check=True, capture_output=True)
     L = C.CDLL(out)
     L.fastmath_probe_f32.argtypes = [C.c_int] + [C.c_void_p] * 4
-    L.fastmath_probe_f64.argtypes = [C.c_int] + [C.c_void_p] * 6
+    L.fastmath_probe_f64.argtypes = [C.c_int] + [C.c_void_p] * 7
     return L
 
 
@@ -59,7 +59,7 @@ def _f32(lib, x):
 def _f64(lib, x):
     import torch
     xt = torch.as_tensor(np.asarray(x, np.float64)).cuda()
-    outs = [torch.empty_like(xt) for _ in range(5)]
+    outs = [torch.empty_like(xt) for _ in range(6)]
     assert lib.fastmath_probe_f64(xt.numel(), xt.data_ptr(), *[o.data_ptr() for o in outs]) == 0
     return [xt.cpu().numpy()] + [o.cpu().numpy() for o in outs]
 
@@ -109,7 +109,7 @@ def test_f64_sincos(lib):
     rng = np.random.default_rng(3)
     x = np.concatenate([rng.uniform(-0.6, np.pi + 0.6, 600), np.logspace(-12, -1, 100),
                         np.pi - np.logspace(-12, -1, 100)])
-    x, s, c, _, _, _ = _f64(lib, x)
+    x, s, c, _, _, _, _ = _f64(lib, x)
     ref = np.array([_exact_sin_cos(v) for v in x])
     assert np.max(np.abs(s - ref[:, 0])) <= 4 * U64
     assert np.max(np.abs(c - ref[:, 1])) <= 4 * U64
@@ -120,16 +120,23 @@ def test_f64_sincos(lib):
 def test_f64_exp_log1p_rcp(lib):
     rng = np.random.default_rng(4)
     xe = np.concatenate([np.linspace(-700.0, 5.0, 7001), rng.uniform(-1.0, 1.0, 1000)])
-    x, _, _, _, e, _ = _f64(lib, xe)
+    x, _, _, _, e, _, _ = _f64(lib, xe)
     ref = np.exp(x)
     assert np.max(np.abs(e - ref) / ref) <= 8 * U64
-    _, _, _, _, e_low, _ = _f64(lib, np.array([-710.0, -750.0, -1e4]))
+    _, _, _, _, e_low, _, _ = _f64(lib, np.array([-710.0, -750.0, -1e4]))
     assert np.all(e_low == 0.0)
     xl = np.logspace(-3, 3, 3001)
-    x, _, _, l, _, _ = _f64(lib, xl)
+    x, _, _, l, _, _, _ = _f64(lib, xl)
     ref = np.array([float(Fraction(math.log1p(v))) for v in x])  # libm log1p, < 1u
     assert np.max(np.abs(l - ref) / ref) <= 8 * U64
     xr = rng.uniform(1.0, 2.0, 3000) * 2.0 ** rng.integers(-30, 30, 3000)
-    x, _, _, _, _, r = _f64(lib, np.concatenate([xr, -xr]))
+    x, _, _, _, _, r, _ = _f64(lib, np.concatenate([xr, -xr]))
     exact = np.array([float(1 / Fraction(v)) for v in x])
     assert np.max(np.abs(r - exact) / np.abs(exact)) <= 4 * U64
+    # reciprocal square root (the launch's 1/|n|): against a 40-digit value
+    from decimal import Decimal, getcontext
+    getcontext().prec = 40
+    xq = xr[:1500] * 1e6
+    x, _, _, _, _, _, q = _f64(lib, xq)
+    exact = np.array([float(1 / Decimal(v).sqrt()) for v in x])
+    assert np.max(np.abs(q - exact) / exact) <= 4 * U64
