@@ -44,7 +44,7 @@ class Problem(C.Structure):
     _fields_ = [
         ("metric", C.c_int32), ("r_in_mode", C.c_int32), ("levels", C.c_int32),
         ("max_steps", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
-        ("pad0", C.c_int32), ("pad1", C.c_int32),
+        ("volumetric", C.c_int32), ("pad1", C.c_int32),
         ("chi", C.c_double), ("lam_E", C.c_double), ("eta", C.c_double), ("lam_c", C.c_double),
         ("r_obs", C.c_double), ("incl", C.c_double),
         ("x_min", C.c_double), ("x_max", C.c_double), ("y_min", C.c_double), ("y_max", C.c_double),
@@ -142,7 +142,7 @@ def _load():
 # Defaults for the readings the paper leaves open (integrator, emissivity
 # constants, thresholds).  Every one is a parameter.
 DEFAULTS = dict(
-    metric=KERR, r_in_mode=0, levels=0, max_steps=1_000_000, nx=64, ny=64,
+    metric=KERR, r_in_mode=0, levels=0, max_steps=1_000_000, nx=64, ny=64, volumetric=0,
     chi=0.5, lam_E=0.1, eta=0.02, lam_c=10.0, r_obs=1000.0, incl=np.deg2rad(17.0),
     x_min=-10.0, x_max=10.0, y_min=-10.0, y_max=10.0,
     j0=1.0, p=2.0, R_s=8.0, sigma_in=0.2, sigma_out=2.0, R_out=20.0, dR_in=0.5, H0=0.05, h=0.05,

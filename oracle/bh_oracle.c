@@ -38,7 +38,9 @@ typedef struct {
   int32_t levels;      /* screen refinement levels, 0..3                  */
   int32_t max_steps;   /* attempted DP5 steps before "undetermined"       */
   int32_t nx, ny;      /* base screen resolution                          */
-  int32_t pad0, pad1;
+  int32_t volumetric;  /* 0: thin-disk events; 1: the volumetric integral
+                          I = int g^3 j(R, theta) dlambda (Eq. 88)        */
+  int32_t pad1;
   double chi;          /* spin a/M (Eq. 1)                                */
   double lam_E;        /* Einasto scale (Eq. 10)                          */
   double eta;          /* cored-NFW 4 pi rho0 r0^2 (Eq. 14)               */
@@ -581,11 +583,43 @@ int orc_dp5_step_dense(int kind, double w, int n, const double* y0, double h, do
 typedef struct {
   const orc_problem* P;
   double E, ell;
+  double num;    /* -p.u_obs (Eq. 89)                                     */
+  double R_in;   /* inner disk edge (Eq. 87 or r_ISCO)                   */
 } orc_geo_ctx;
 
+/* Source of the volumetric intensity (Eq. 88): g^3 j(R, theta) with the
+ * emissivity of Eqs. (83)-(86) at (R, theta) and, as the reading of the
+ * emitter's motion off the plane, the circular emitter of Eqs. (90)-(91) at
+ * the cylindrical radius rho = R sin(theta) of the equatorial metric; zero
+ * where no timelike circular orbit exists there. */
+static double orc_vol_source(const orc_geo_ctx* g, double R, double th) {
+  double rho = R * sin(th), W, uT;
+  if (!(rho > 0.0) || orc_circular(g->P, rho, &W, &uT) != 0) return 0.0;
+  double gfac = g->num / (-uT * ((-g->E) + W * g->ell));
+  return gfac * gfac * gfac * orc_emissivity(g->P, g->R_in, R, th);
+}
+
+/* Volumetric mode only (reading): a step that may come within 5 H(rho) of
+ * the equatorial plane advances z = R cos(theta) by at most H(rho) / 2, so
+ * that the stages sample the Gaussian layer of Eq. (83) however thin it is
+ * (error control alone can step over a layer that no stage lands in). */
+static double orc_layer_cap(const orc_problem* P, const double* y, const double* f, double h) {
+  double c = cos(y[2]), s = sin(y[2]);
+  double z = y[1] * c, zd = f[1] * c - y[1] * s * f[2];
+  double Hc = P->H0 + P->h * fabs(y[1] * s);               /* Eq. (84) */
+  if (fabs(zd) > 0.0 && fabs(z) - fabs(zd) * h < 5.0 * Hc) {
+    double cap = 0.5 * Hc / fabs(zd);
+    if (h > cap) h = cap;
+  }
+  return h;
+}
+
+/* Hamilton's equations (Eqs. 57-62); in volumetric mode a seventh
+ * component carries the accumulated intensity, d I / d lambda = g^3 j. */
 static void orc_geo_rhs(void* c, const double* y, double* dy) {
   orc_geo_ctx* g = (orc_geo_ctx*)c;
   orc_rhs(g->P, g->E, g->ell, y, dy);
+  if (g->P->volumetric) dy[6] = orc_vol_source(g, y[1], y[2]);
 }
 
 /* A stage is admissible only outside the horizon (Delta > 0); otherwise
@@ -630,7 +664,7 @@ static int orc_trace_ray_core(const orc_problem* P, const orc_geom* G, double X,
   memset(out, 0, sizeof(*out));
   out->near_thdot = INFINITY;
   out->near_dlam = INFINITY;
-  double y[6], u_o[4], E, ell;
+  double y[7], u_o[4], E, ell;
   orc_launch(P, X, Y, y, &E, &ell, u_o, NULL);
   out->E = E;
   out->ell = ell;
@@ -638,10 +672,16 @@ static int orc_trace_ray_core(const orc_problem* P, const orc_geom* G, double X,
   /* Redshift numerator -p.u_obs (Eq. 89); equals E_loc = 1 by construction. */
   double num = -((-E) * u_o[0] + ell * u_o[3]);
 
-  orc_geo_ctx ctx = {P, E, ell};
-  double k[7][ORC_NMAX], y1[6], err[6];
+  orc_geo_ctx ctx = {P, E, ell, num, G->R_in};
+  /* reading: in volumetric mode the intensity is a seventh ODE component,
+   * integrated by the same Dormand-Prince steps and included in the error
+   * norm (RMS over the seven components) */
+  const int nc = P->volumetric ? 7 : 6;
+  double k[7][ORC_NMAX], y1[7], err[7];
+  y[6] = 0.0;
   orc_geo_rhs(&ctx, y, k[0]);
-  double h = orc_initial_step(orc_geo_rhs, &ctx, 6, y, k[0], P->rtol, P->atol);
+  double h = orc_initial_step(orc_geo_rhs, &ctx, nc, y, k[0], P->rtol, P->atol);
+  if (P->volumetric) h = orc_layer_cap(P, y, k[0], h);
   double lam = 0.0, lam_last = -INFINITY;
   int rejected = 0, have_trusted = 0;
   out->R_min = y[1];
@@ -654,9 +694,9 @@ static int orc_trace_ray_core(const orc_problem* P, const orc_geom* G, double X,
       if (out->n_accept >= nplay) break;
       h = hplay[out->n_accept];
     }
-    int bad = orc_dp5_trial(orc_geo_rhs, orc_geo_valid, &ctx, 6, y, h, k, y1, err);
+    int bad = orc_dp5_trial(orc_geo_rhs, orc_geo_valid, &ctx, nc, y, h, k, y1, err);
     if (bad && !hplay) { h *= 0.5; rejected = 1; out->n_reject++; continue; }
-    double e = orc_err_norm(6, y, y1, err, P->rtol, P->atol);
+    double e = orc_err_norm(nc, y, y1, err, P->rtol, P->atol);
     if (!hplay && !(e <= 1.0)) {
       h *= orc_step_factor(e, 1);
       rejected = 1;
@@ -708,7 +748,9 @@ static int orc_trace_ray_core(const orc_problem* P, const orc_geom* G, double X,
           gfac = num / den;
           jem = orc_emissivity(P, G->R_in, Rc, half_pi);
         }
-        double In = gfac * gfac * gfac * jem;      /* thin-disk g^3 j (reading of Eq. 88) */
+        /* thin-disk g^3 j (reading of Eq. 88); the volumetric mode adds no
+         * event intensity (its integral is the seventh component) */
+        double In = P->volumetric ? 0.0 : gfac * gfac * gfac * jem;
         out->I_tot += In;
         if (n < 3) {
           double ph = fmod(yc[3], 2.0 * M_PI);
@@ -727,7 +769,7 @@ static int orc_trace_ray_core(const orc_problem* P, const orc_geom* G, double X,
       }
     }
     lam += h;
-    for (int i = 0; i < 6; ++i) { y[i] = y1[i]; k[0][i] = k[6][i]; }
+    for (int i = 0; i < nc; ++i) { y[i] = y1[i]; k[0][i] = k[6][i]; }
     /* Polar axis (reading): a ray that passed through theta = 0 or pi is
      * mapped back to (0, pi) by (theta, p_theta, phi) -> (-theta, -p_theta,
      * phi + pi) or (2 pi - theta, -p_theta, phi + pi). */
@@ -753,8 +795,10 @@ static int orc_trace_ray_core(const orc_problem* P, const orc_geom* G, double X,
     if (y[1] < G->R_cap) { out->status = 1; break; }     /* Eq. (75) */
     if (y[1] > G->R_esc) { out->status = 0; break; }     /* escape, Sec. 3.3 */
     h *= orc_step_factor(e, rejected);
+    if (P->volumetric) h = orc_layer_cap(P, y, k[0], h);
     rejected = 0;
   }
+  if (P->volumetric) out->I_tot = y[6];
   out->R_final = y[1];
   out->lam_final = lam;
   out->K_final = orc_carter(P, E, ell, y[2], y[5]);
