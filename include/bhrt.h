@@ -94,11 +94,21 @@ typedef struct {
                               cells per base pixel                          */
 } bh_camera;
 
-/* Emission (Sec. 5.1, Eqs. 83-87).  The thin-disk path evaluates j on the
- * equatorial plane (z = 0), so H0 and h only matter for off-plane use. */
+/* Emission (Sec. 5.1, Eqs. 83-87).  The default thin-disk mode evaluates j
+ * on the equatorial plane (z = 0) at each trusted crossing, so H0 and h only
+ * matter in the volumetric mode. */
 typedef struct {
   int32_t r_in_mode;  /* 0: R_in = r_ISCO (prograde); 1: R_in = R_+ + dR_in (Eq. 87) */
-  int32_t reserved;   /* must be 0 */
+  int32_t volumetric; /* 0: thin disk, I = sum over crossings of g^3 j(R_em, 0);
+                         1: the finite-thickness integral of Eq. (88),
+                         I = int g^3 j(R, theta) dlambda, integrated as a
+                         seventh component of the Dormand-Prince system
+                         (in its error norm), with the circular emitter at
+                         the cylindrical radius rho (Eqs. 90-91), j = 0 where
+                         no timelike orbit exists, and steps that may come
+                         within 5 H of the plane advancing z by at most H/2.
+                         I_n planes stay 0; H0 > 0 and h >= 0 required.
+                         Not differentiable by bh_trace_backward.          */
   double j0, p, R_s;  /* normalisation, radial power, radial scale (Eq. 83) */
   double sigma_in, sigma_out, R_out; /* tapers, Eqs. (85)-(86)             */
   double dR_in;       /* used when r_in_mode == 1                           */

@@ -593,10 +593,13 @@ typedef struct {
  * the cylindrical radius rho = R sin(theta) of the equatorial metric; zero
  * where no timelike circular orbit exists there. */
 static double orc_vol_source(const orc_geo_ctx* g, double R, double th) {
-  double rho = R * sin(th), W, uT;
+  /* a trial stage past the polar axis (theta < 0 or > pi) is the point at
+   * the mirrored angle: same rho = R |sin theta| and z^2 */
+  double thr = th < 0.0 ? -th : (th > M_PI ? 2.0 * M_PI - th : th);
+  double rho = R * sin(thr), W, uT;
   if (!(rho > 0.0) || orc_circular(g->P, rho, &W, &uT) != 0) return 0.0;
   double gfac = g->num / (-uT * ((-g->E) + W * g->ell));
-  return gfac * gfac * gfac * orc_emissivity(g->P, g->R_in, R, th);
+  return gfac * gfac * gfac * orc_emissivity(g->P, g->R_in, R, thr);
 }
 
 /* Volumetric mode only (reading): a step that may come within 5 H(rho) of
@@ -606,7 +609,7 @@ static double orc_vol_source(const orc_geo_ctx* g, double R, double th) {
 static double orc_layer_cap(const orc_problem* P, const double* y, const double* f, double h) {
   double c = cos(y[2]), s = sin(y[2]);
   double z = y[1] * c, zd = f[1] * c - y[1] * s * f[2];
-  double Hc = P->H0 + P->h * fabs(y[1] * s);               /* Eq. (84) */
+  double Hc = P->H0 + P->h * fabs(y[1] * s);               /* Eq. (84), rho = R |sin| */
   if (fabs(zd) > 0.0 && fabs(z) - fabs(zd) * h < 5.0 * Hc) {
     double cap = 0.5 * Hc / fabs(zd);
     if (h > cap) h = cap;

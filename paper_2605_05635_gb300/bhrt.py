@@ -48,7 +48,7 @@ class _Camera(C.Structure):
 
 
 class _Emission(C.Structure):
-    _fields_ = [("r_in_mode", C.c_int32), ("reserved", C.c_int32), ("j0", C.c_double),
+    _fields_ = [("r_in_mode", C.c_int32), ("volumetric", C.c_int32), ("j0", C.c_double),
                 ("p", C.c_double), ("R_s", C.c_double), ("sigma_in", C.c_double),
                 ("sigma_out", C.c_double), ("R_out", C.c_double), ("dR_in", C.c_double),
                 ("H0", C.c_double), ("h", C.c_double)]
@@ -149,10 +149,11 @@ class Emission:
     dR_in: float = 0.5
     H0: float = 0.05
     h: float = 0.05
+    volumetric: int = 0
 
     def _c(self):
-        return _Emission(self.r_in_mode, 0, self.j0, self.p, self.R_s, self.sigma_in,
-                         self.sigma_out, self.R_out, self.dR_in, self.H0, self.h)
+        return _Emission(self.r_in_mode, self.volumetric, self.j0, self.p, self.R_s,
+                         self.sigma_in, self.sigma_out, self.R_out, self.dR_in, self.H0, self.h)
 
 
 @dataclasses.dataclass
@@ -189,7 +190,8 @@ def from_flat(d: dict):
     em = Emission(r_in_mode=d.get("r_in_mode", 0), j0=d.get("j0", 1.0), p=d.get("p", 2.0),
                   R_s=d.get("R_s", 8.0), sigma_in=d.get("sigma_in", 0.2),
                   sigma_out=d.get("sigma_out", 2.0), R_out=d.get("R_out", 20.0),
-                  dR_in=d.get("dR_in", 0.5), H0=d.get("H0", 0.05), h=d.get("h", 0.05))
+                  dR_in=d.get("dR_in", 0.5), H0=d.get("H0", 0.05), h=d.get("h", 0.05),
+                  volumetric=d.get("volumetric", 0))
     it = Integrator(precision=d.get("precision", FP64), max_steps=d.get("max_steps", 1_000_000),
                     rtol=d.get("rtol", 1e-10), atol=d.get("atol", 1e-12),
                     cap_factor=d.get("cap_factor", 1.01), esc_factor=d.get("esc_factor", 1.1),

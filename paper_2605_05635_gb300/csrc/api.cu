@@ -179,7 +179,10 @@ bh_status validate(const bh_spacetime& s, const bh_camera& c, const bh_emission&
   if (c.refine_levels < 0 || c.refine_levels > kMaxLevels || c.refine_capacity < 0)
     return BH_ERR_INVALID_ARG;
   if ((int64_t)c.nx * c.ny > (int64_t(1) << 40)) return BH_ERR_INVALID_ARG;
-  if (e.r_in_mode < 0 || e.r_in_mode > 1 || e.reserved != 0) return BH_ERR_INVALID_ARG;
+  if (e.r_in_mode < 0 || e.r_in_mode > 1 || e.volumetric < 0 || e.volumetric > 1)
+    return BH_ERR_INVALID_ARG;
+  if (e.volumetric && !(finite_pos(e.H0) && e.h >= 0.0 && std::isfinite(e.h)))
+    return BH_ERR_INVALID_ARG;
   if (!finite_pos(e.R_s) || !finite_pos(e.sigma_in) || !finite_pos(e.sigma_out) ||
       !std::isfinite(e.j0) || !std::isfinite(e.p) || !std::isfinite(e.R_out))
     return BH_ERR_INVALID_ARG;
@@ -249,6 +252,16 @@ bh_status make_params(const bh_spacetime& s, const bh_camera& c, const bh_emissi
   ip.sig_in = e.sigma_in;
   ip.sig_out = e.sigma_out;
   ip.R_out = e.R_out;
+  ip.H0 = e.H0;
+  ip.hh = e.h;
+  ip.volumetric = e.volumetric;
+  ip.isig_in = 1.0 / e.sigma_in;
+  ip.isig_out = 1.0 / e.sigma_out;
+  ip.iR_s = 1.0 / e.R_s;
+  ip.iR_in = 1.0 / ip.R_in;
+  const double vf[10] = {e.H0, e.h, ip.R_in, ip.isig_in, ip.isig_out, e.R_out, e.p, ip.iR_s,
+                         e.j0, ip.iR_in};
+  for (int k = 0; k < 10; ++k) ip.vf[k] = (float)vf[k];
   ip.rtol = g.rtol;
   ip.atol = g.atol;
   ip.thdot_min = g.thetadot_min;
@@ -362,6 +375,7 @@ struct bh_plan_s {
   LaunchShape shape64{0, 128};  // FP64 promoted pass of the mixed path
   int refine_blocks = 0;
   bool any_keys = false;
+  bool any_vol = false;   // some image integrates the volumetric intensity
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
   bool timing = false;                       // events around the trace launches
@@ -417,6 +431,7 @@ bh_status plan_build(int32_t n, const bh_spacetime* st, const bh_camera* cam,
     d.steps = o.steps;
     d.promoted = o.promoted;
     if (d.keys_count) p.any_keys = true;
+    if (em[i].volumetric) p.any_vol = true;
     if (integ[i].time_budget_s > budget) budget = integ[i].time_budget_s;
   }
   p.budget_ns = (unsigned long long)(budget * 1e9);
@@ -445,6 +460,7 @@ TraceArgs trace_args(const bh_plan_s& p, int level) {
   a.mode = 0;
   a.npix = p.npix;
   a.n_items = (int64_t)p.n * p.npix;
+  a.any_volumetric = p.any_vol ? 1 : 0;
   a.base_I = reinterpret_cast<double*>(p.ws + p.L.base_I);
   a.base_cls = reinterpret_cast<uint16_t*>(p.ws + p.L.base_cls);
   a.base_depth = reinterpret_cast<uint8_t*>(p.ws + p.L.base_depth);
@@ -684,6 +700,7 @@ bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh
   a.head = &hdr->head[0];
   a.source = 0;
   a.allow_spill = 0;  // points mode: the mixed kernel runs without promotion
+  a.any_volumetric = em->volumetric;
   LaunchShape sh{num_sms() * trace_default_blocks_per_sm(integ->precision, 128), 128};
   cudaError_t e = integ->precision == 0 ? launch_trace_fp64(a, sh, cs) : launch_trace_mixed(a, sh, cs);
   return e == cudaSuccess ? BH_OK : BH_ERR_CUDA;
@@ -1052,6 +1069,7 @@ bh_status bh_trace_backward(const bh_spacetime* st, const bh_camera* cam, const 
                             double* diag11, float* image_out, void* workspace,
                             size_t workspace_bytes, void* stream) {
   if (!st || !cam || !em || !integ || !grad10) return BH_ERR_INVALID_ARG;
+  if (em->volumetric) return BH_ERR_INVALID_ARG;  // the adjoint covers the thin-disk events
   BwdLayout BL;
   if (!bwd_layout(*cam, BL)) return BH_ERR_INVALID_ARG;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < BL.total)

@@ -169,6 +169,45 @@ __device__ __forceinline__ double emissivity_eq(const ImgParams& ip, double R) {
   return ip.j0 * pow(R / ip.R_in, -ip.p) * exp(-(R - ip.R_in) / ip.R_s) * tin * tout;
 }
 
+// Source of the volumetric intensity, Eq. (88): g^3 j at (R, theta) with the
+// emissivity of Eqs. (83)-(86) (rho = R |sin theta|, z = R cos theta, so a
+// trial stage past the polar axis is its mirror point) and the circular
+// emitter of Eqs. (90)-(91) at the cylindrical radius rho of the equatorial
+// metric (reading); 0 where no timelike circular orbit exists there.  The
+// tapers are written 0.5 (1 + tanh a) = 1 / (1 + exp(-2 a)).
+static __device__ __noinline__ double vol_source64(const ImgParams& ip, MetricConsts<double> m,
+                                                   double E, double ell, double R, double th) {
+  double s, c;
+  d_sincos(th, &s, &c);
+  const double rho = R * fabs(s), z = R * c;
+  double g;
+  if (!(rho > 0.0) || !emitter_g(m, rho, E, ell, g)) return 0.0;
+  const double Hd = ip.H0 + ip.hh * rho;                        // Eq. (84)
+  const double iH = d_rcp(Hd);
+  const double tin = d_rcp(1.0 + d_exp(-2.0 * (rho - ip.R_in) * ip.isig_in));    // Eq. (85)
+  const double tout = d_rcp(1.0 + d_exp(2.0 * (rho - ip.R_out) * ip.isig_out));  // Eq. (86)
+  const double lnj = -ip.p * d_log1p(rho * ip.iR_in - 1.0) - (rho - ip.R_in) * ip.iR_s -
+                     0.5 * (z * iH) * (z * iH);                 // Eq. (83)
+  return g * g * g * ip.j0 * d_exp(lnj) * tin * tout;
+}
+
+// Volumetric mode (reading, as in the oracle): a step that may come within
+// 5 H(rho) of the equatorial plane advances z by at most H(rho) / 2, so
+// that the stages sample the Gaussian layer however thin it is.
+template <class T>
+__device__ __forceinline__ T layer_cap(T H0, T hh, T R, T th, T fR, T fth, T h) {
+  T s, c;
+  d_sincos(th, &s, &c);
+  const T z = R * c, zd = fR * c - R * s * fth;
+  const T Hc = H0 + hh * fabs(R * s);
+  const T azd = fabs(zd);
+  if (azd > T(0) && fabs(z) - azd * h < T(5) * Hc) {
+    const T cap = T(0.5) * Hc * d_rcp(azd);
+    if (h > cap) h = cap;
+  }
+  return h;
+}
+
 // Event bookkeeping common to both precisions.
 struct CrossState {
   double I[4];      // I_tot, I_0, I_1, I_2
@@ -236,7 +275,8 @@ static __device__ __noinline__ void handle_crossing(const ImgParams& ip, const M
   int n = cs.ncross;
   double g = 0.0, j = 0.0;
   if (emitter_g(m, yc[1], E, ell, g)) j = emissivity_eq(ip, yc[1]);
-  double In = g * g * g * j;
+  // the volumetric mode adds no event intensity (its integral is a state)
+  double In = ip.volumetric ? 0.0 : g * g * g * j;
   cs.I[0] += In;
   if (n < 3) {
     cs.I[1 + n] = In;
@@ -286,6 +326,7 @@ __device__ __forceinline__ void rhs_f64_into(const MetricConsts<double>& m, doub
 struct Ray64 {
   double y[6];     // T, R, th, phi, p_R, p_th
   double f[6];     // f(y) (FSAL)
+  double fI;       // volumetric source g^3 j at y (FSAL of the seventh component)
   double h, lam;
   double E, ell;
   CrossState cs;
@@ -311,6 +352,7 @@ __device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricCons
   r.ell = ip.sq_gph * (-X * id);
   r.E = ip.zamo_N + ip.zamo_w * r.ell;
   rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
+  r.fI = ip.volumetric ? vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]) : 0.0;
   // starting-step heuristic in FP32 (it only needs a few digits)
   float d0 = 0.f, d1 = 0.f, sc[6];
 #pragma unroll
@@ -337,6 +379,8 @@ __device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricCons
   const float mx = fmaxf(d1, d2);
   const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : __powf(__fdividef(0.01f, mx), 0.2f);
   r.h = (double)fminf(100.f * h0, h1);
+  if (ip.volumetric)
+    r.h = layer_cap(ip.H0, ip.hh, r.y[1], r.y[2], r.f[1], r.f[2], r.h);
   r.lam = 0.0;
   r.cs.lam_last = 0.0;
   r.cs.have_trusted = false;
@@ -402,6 +446,9 @@ __device__ __forceinline__ float err_term(double y0, double y1, double he, float
   return q * q;
 }
 
+// kVol: the build that can integrate the volumetric intensity (Eq. 88) as a
+// seventh component; the thin-disk build carries none of its registers.
+template <bool kVol>
 __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConsts<double>& m,
                                           Ray64& r, const TraceArgs& a, int64_t item,
                                           uint32_t img) {
@@ -423,6 +470,10 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     for (int x = 0; x < 4; ++x) q[u][x] = 0.0;
   bool bad = false;
   double W = 0, P2oD = 1;
+  // volumetric mode: the intensity integral is a seventh component whose
+  // derivative g^3 j depends on the state only (kI, sums s5I and seI)
+  const bool vol = kVol && ip.volumetric != 0;
+  double kI = kVol ? r.fI : 0.0, s5I = 0.0, seI = 0.0;
 #pragma unroll 1
   for (int j = 0; j < 7; ++j) {
     // zero coefficients (about a third of the triangular sums) are skipped
@@ -431,11 +482,13 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
       const double bj = kDPr.b[j];
 #pragma unroll
       for (int i = 0; i < 6; ++i) s5[i] = fma(bj, k[i], s5[i]);
+      s5I = fma(bj, kI, s5I);
     }
     if ((kDPr.emask >> j) & 1) {
       const double ej = kDPr.e[j];
 #pragma unroll
       for (int i = 0; i < 6; ++i) se[i] = fma(ej, k[i], se[i]);
+      seI = fma(ej, kI, seI);
     }
     if ((kDPr.dmask >> j) & 1) {
       const double dj = kDPr.d[j];
@@ -457,6 +510,7 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     for (int x = 0; x < 4; ++x) ys[x] = r.y[kQC(x)] + h * q[0][x];
     bool ok = geo_rhs(m, r.E, r.ell, ys[0], ys[1], ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
+    if (vol) kI = vol_source64(ip, m, r.E, r.ell, ys[0], ys[1]);
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
 #pragma unroll
@@ -473,7 +527,9 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     y1[i] = r.y[i] + h * s5[i];
     err2 += err_term(r.y[i], y1[i], h * se[i], fatol, frtol);
   }
-  float err = sqrtf(err2 / 6.f);
+  const double I1 = r.cs.I[0] + h * s5I;
+  if (vol) err2 += err_term(r.cs.I[0], I1, h * seI, fatol, frtol);
+  float err = sqrtf(err2 / (vol ? 7.f : 6.f));
   r.steps++;
   if (bad || !(err <= 1.f)) {
     r.h = bad ? 0.5 * h : h * (double)step_factor(err, true);
@@ -482,6 +538,10 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     return r.steps >= ip.max_steps ? 3 : 0;
   }
   r.nacc++;
+  if (vol) {
+    r.cs.I[0] = I1;
+    r.fI = kI;
+  }
   {
     const double s0 = r.y[2] - kHalfPi, s1 = y1[2] - kHalfPi;
     if ((s0 > 0.0 && s1 <= 0.0) || (s0 < 0.0 && s1 >= 0.0)) {
@@ -509,14 +569,17 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     r.y[i] = y1[i];
     r.f[i] = k[i];
   }
-  if (reflect_axis(r.y[2], r.y[5], r.y[3]))
+  if (reflect_axis(r.y[2], r.y[5], r.y[3])) {
     rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
+    if (vol) r.fI = vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]);
+  }
   // null-constraint monitor at the new point (stage 7 = new point, FSAL)
   float hdv = (float)(fabs(W) / P2oD);
   if (hdv > r.hdrift) r.hdrift = hdv;
   if (r.y[1] < ip.R_cap) return 2;
   if (r.y[1] > ip.R_esc) return 1;
   r.h = h * (double)step_factor(err, r.rejected);
+  if (vol) r.h = layer_cap(ip.H0, ip.hh, r.y[1], r.y[2], r.f[1], r.f[2], r.h);
   r.rejected = false;
   return r.steps >= ip.max_steps ? 3 : 0;
 }
@@ -557,8 +620,8 @@ __device__ __forceinline__ void spill_from64(const Ray64& r, int64_t item, uint3
   s.pad = 0;
 }
 
-__device__ __forceinline__ void resume64(const SpillRec& s, const MetricConsts<double>& m,
-                                         Ray64& r) {
+__device__ __forceinline__ void resume64(const ImgParams& ip, const SpillRec& s,
+                                         const MetricConsts<double>& m, Ray64& r) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) r.y[i] = s.y[i];
   r.h = s.h;
@@ -576,6 +639,7 @@ __device__ __forceinline__ void resume64(const SpillRec& s, const MetricConsts<d
   r.nrej = s.nrej;
   r.steps = s.steps;
   rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
+  r.fI = ip.volumetric ? vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]) : 0.0;
 }
 
 // Resolves a fresh work item to its image, output pixel and screen point.

@@ -55,6 +55,8 @@ struct TraceArgs {
   unsigned long long* spill_out_count;
   int64_t spill_cap;
   int allow_spill;                    // FP32: promote; FP64: demote
+  int any_volumetric;                 // some image integrates Eq. (88): use the
+                                      // kernel build that carries the integral
 };
 
 struct LaunchShape {

@@ -23,8 +23,9 @@ namespace bhrt {
 
 // MinBlocks = 0 leaves the register count to the compiler (2 blocks of 128
 // threads per SM); MinBlocks = 3 caps it for 3 blocks at a small spill cost.
-// The autotuner picks between them.
-template <int MinBlocks>
+// The autotuner picks between them.  Vol = true is the build used when some
+// image of the call integrates the volumetric intensity.
+template <int MinBlocks, bool Vol>
 __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t n_items = pass_items(a);
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
           img = s.img;
           ip = &a.ip[img];
           m = metric_consts<double>(*ip);
-          resume64(s, m, r);
+          resume64(*ip, s, m, r);
         } else {
           double X, Y;
           int64_t pix;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
     w_lanes += (unsigned long long)__popc(am);
     if (active) {
       const int acc0 = r.nacc, rej0 = r.nrej;
-      int term = ray_step64(*ip, m, r, a, item, img);
+      int term = ray_step64<Vol>(*ip, m, r, a, item, img);
       w_acc += (unsigned long long)(r.nacc - acc0);
       w_rej += (unsigned long long)(r.nrej - rej0);
       if (term) {
@@ -119,17 +120,24 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
 }
 
 cudaError_t launch_trace_fp64(const TraceArgs& a, LaunchShape s, cudaStream_t st) {
-  if (s.variant == 1)
-    trace_fp64_kernel<3><<<s.blocks, s.threads, 0, st>>>(a);
-  else
-    trace_fp64_kernel<0><<<s.blocks, s.threads, 0, st>>>(a);
+  if (a.any_volumetric) {
+    if (s.variant == 1)
+      trace_fp64_kernel<3, true><<<s.blocks, s.threads, 0, st>>>(a);
+    else
+      trace_fp64_kernel<0, true><<<s.blocks, s.threads, 0, st>>>(a);
+  } else if (s.variant == 1) {
+    trace_fp64_kernel<3, false><<<s.blocks, s.threads, 0, st>>>(a);
+  } else {
+    trace_fp64_kernel<0, false><<<s.blocks, s.threads, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
 size_t spill_record_bytes() { return sizeof(SpillRec); }
 
 const void* trace_fp64_kernel_ptr(int variant) {
-  return variant == 1 ? (const void*)trace_fp64_kernel<3> : (const void*)trace_fp64_kernel<0>;
+  return variant == 1 ? (const void*)trace_fp64_kernel<3, false>
+                      : (const void*)trace_fp64_kernel<0, false>;
 }
 
 }  // namespace bhrt

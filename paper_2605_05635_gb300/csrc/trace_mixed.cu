@@ -63,6 +63,52 @@ __device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, float
   for (int i = 0; i < 6; ++i) d[i] = o.d[i];
 }
 
+// Redshift of a prograde circular emitter (Eqs. 89-91), FP32.
+__device__ __forceinline__ bool emitter_g_f(const MetricConsts<float>& m, float R, float E,
+                                            float ell, float& g) {
+  float H, dH;
+  lapse(m, R, 1.f / R, H, dH);
+  const float den = 2.f * R - m.chi2 * dH, disc = 2.f * R * dH;
+  if (!(disc >= 0.f) || den == 0.f) return false;
+  const float W = (-m.chi * dH + sqrtf(disc)) / den;
+  const float gtt = -H, gtp = -m.chi * (1.f - H), gpp = R * R + m.chi2 + m.chi2 * (1.f - H);
+  const float norm = -(gtt + 2.f * W * gtp + W * W * gpp);
+  if (!(norm > 0.f)) return false;
+  g = sqrtf(norm) / (E - W * ell);
+  return true;
+}
+
+// pi/2 as a float pair hi + lo, and pi (hi part) for the axis test.
+constexpr float kHalfPiHi = 1.57079637050628662109375f;
+constexpr float kHalfPiLo = -4.37113900018624283e-8f;
+constexpr float kPiHi = 3.1415927410125732421875f;
+
+// theta - pi/2 from the float pair (hi + lo + extra), exact to the rounding
+// of the small terms: the height z = -R sin(theta - pi/2) inside a thin layer
+// keeps its relative accuracy, which theta rounded to one float would not.
+__device__ __forceinline__ float dtheta_eq(float th_h, float th_l, float extra) {
+  return __fadd_rn(__fsub_rn(th_h, kHalfPiHi), __fsub_rn(th_l, kHalfPiLo) + extra);
+}
+
+// Source of the volumetric intensity (Eq. 88) in FP32: g^3 j at (R, theta),
+// theta given as dth = theta - pi/2 (see dtheta_eq), as vol_source64 (mirror
+// point past the polar axis, emitter at the cylindrical radius rho, tapers as
+// logistic functions), from the image's FP32 emission constants.
+static __device__ __noinline__ float vol_source32(const ImgParams& ip, MetricConsts<float> m,
+                                                  float E, float ell, float R, float dth) {
+  float s, c;
+  d_sincos(dth, &s, &c);
+  const float rho = R * fabsf(c), z = -R * s;
+  float g;
+  if (!(rho > 0.f) || !emitter_g_f(m, rho, E, ell, g)) return 0.f;
+  const float* v = ip.vf;  // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
+  const float zH = __fdividef(z, v[0] + v[1] * rho);                    // Eq. (84)
+  const float tin = __fdividef(1.f, 1.f + __expf(-2.f * (rho - v[2]) * v[3]));   // Eq. (85)
+  const float tout = __fdividef(1.f, 1.f + __expf(2.f * (rho - v[5]) * v[4]));   // Eq. (86)
+  const float lnj = -v[6] * __logf(rho * v[9]) - (rho - v[2]) * v[7] - 0.5f * zH * zH;
+  return g * g * g * v[8] * __expf(lnj) * tin * tout;                    // Eq. (83)
+}
+
 struct RayMx {
   float yh[6], yl[6];  // state T, R, th, phi, p_R, p_th as hi + lo
   float f[6];          // f(y) in FP32 (FSAL)
@@ -71,30 +117,12 @@ struct RayMx {
   double E, ell;
   float Ef, ellf;
   CrossState cs;
+  float fI;            // volumetric source at the state (FSAL of the seventh component)
+  float Ih, Il;        // volumetric intensity so far as hi + lo (cs.I[0] at hand-off)
   float hdrift;
   int32_t nacc, nrej, steps;
   bool rejected;
 };
-
-__device__ __forceinline__ void mx_from64(const Ray64& r, RayMx& x) {
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    df_from(r.y[i], x.yh[i], x.yl[i]);
-    x.f[i] = (float)r.f[i];
-  }
-  x.h = (float)r.h;
-  df_from(r.lam, x.lh, x.ll);
-  x.E = r.E;
-  x.ell = r.ell;
-  x.Ef = (float)r.E;
-  x.ellf = (float)r.ell;
-  x.cs = r.cs;
-  x.hdrift = r.hdrift;
-  x.nacc = r.nacc;
-  x.nrej = r.nrej;
-  x.steps = r.steps;
-  x.rejected = r.rejected;
-}
 
 __device__ __forceinline__ void mx_spill(const RayMx& x, int64_t item, uint32_t img,
                                          SpillRec& s) {
@@ -118,8 +146,9 @@ __device__ __forceinline__ void mx_spill(const RayMx& x, int64_t item, uint32_t 
   s.pad = 0;
 }
 
-__device__ __forceinline__ void mx_resume(const SpillRec& s, const MetricConsts<float>& mf,
-                                          RayMx& x) {
+template <bool kVol>
+__device__ __forceinline__ void mx_resume(const ImgParams& ip, const SpillRec& s,
+                                          const MetricConsts<float>& mf, RayMx& x) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) df_from(s.y[i], x.yh[i], x.yl[i]);
   x.h = (float)s.h;
@@ -139,6 +168,12 @@ __device__ __forceinline__ void mx_resume(const SpillRec& s, const MetricConsts<
   x.nrej = s.nrej;
   x.steps = s.steps;
   rhs_f32_into(mf, x.Ef, x.ellf, x.yh[1], x.yh[2], x.yh[4], x.yh[5], x.f);
+  if (kVol) {
+    df_from(s.I[0], x.Ih, x.Il);
+    x.fI = ip.volumetric
+               ? vol_source32(ip, mf, x.Ef, x.ellf, x.yh[1], dtheta_eq(x.yh[2], x.yl[2], 0.f))
+               : 0.f;
+  }
 }
 
 struct MxConsts {
@@ -149,6 +184,7 @@ struct MxConsts {
 // Launch of the mixed path: the constants of motion and the launch momenta
 // in FP64 (Eqs. 70-74, as in ray_init64), the state as float pairs, and the
 // Hairer-Wanner starting step in FP32.
+template <bool kVol>
 __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricConsts<float>& mf,
                                             const MxConsts& c, double X, double Y, RayMx& r) {
   const double id = d_rsqrt(ip.r_obs * ip.r_obs + X * X + Y * Y);
@@ -187,6 +223,12 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   const float mx = fmaxf(d1, d2);
   const float h1 = (mx <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : __powf(__fdividef(0.01f, mx), 0.2f);
   r.h = fminf(100.f * h0, h1);
+  r.fI = 0.f;
+  r.Ih = r.Il = 0.f;
+  if (kVol && ip.volumetric) {
+    r.fI = vol_source32(ip, mf, r.Ef, r.ellf, r.yh[1], dtheta_eq(r.yh[2], r.yl[2], 0.f));
+    r.h = layer_cap(ip.vf[0], ip.vf[1], r.yh[1], r.yh[2], r.f[1], r.f[2], r.h);
+  }
   r.lh = r.ll = 0.f;
   r.cs.lam_last = 0.0;
   r.cs.have_trusted = false;
@@ -195,21 +237,6 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   r.rejected = false;
   r.nacc = r.nrej = r.steps = 0;
   r.hdrift = 0.f;
-}
-
-// Redshift of a prograde circular emitter (Eqs. 89-91), FP32.
-__device__ __forceinline__ bool emitter_g_f(const MetricConsts<float>& m, float R, float E,
-                                            float ell, float& g) {
-  float H, dH;
-  lapse(m, R, 1.f / R, H, dH);
-  const float den = 2.f * R - m.chi2 * dH, disc = 2.f * R * dH;
-  if (!(disc >= 0.f) || den == 0.f) return false;
-  const float W = (-m.chi * dH + sqrtf(disc)) / den;
-  const float gtt = -H, gtp = -m.chi * (1.f - H), gpp = R * R + m.chi2 + m.chi2 * (1.f - H);
-  const float norm = -(gtt + 2.f * W * gtp + W * W * gpp);
-  if (!(norm > 0.f)) return false;
-  g = sqrtf(norm) / (E - W * ell);
-  return true;
 }
 
 // Crossing inside an accepted FP32 step: the rule of handle_crossing with an
@@ -270,7 +297,8 @@ static __device__ __noinline__ void cross_f32(const ImgParams& ip, const MetricC
     j = (float)ip.j0 * exp2f(-(float)ip.p * log2f(Rc / Rin)) * __expf(-(Rc - Rin) / (float)ip.R_s) *
         tin * tout;
   }
-  const float In = g * g * g * j;
+  // the volumetric mode adds no event intensity (its integral is a state)
+  const float In = ip.volumetric ? 0.f : g * g * g * j;
   cs.I[0] += (double)In;
   if (n < 3) {
     cs.I[1 + n] = (double)In;
@@ -295,13 +323,10 @@ static __device__ __noinline__ void cross_f32(const ImgParams& ip, const MetricC
   cs.have_trusted = true;
 }
 
-// pi/2 as a float pair hi + lo, and pi (hi part) for the axis test.
-constexpr float kHalfPiHi = 1.57079637050628662109375f;
-constexpr float kHalfPiLo = -4.37113900018624283e-8f;
-constexpr float kPiHi = 3.1415927410125732421875f;
-
 // One attempted FP32 step.  Returns 0 (continue), terminal status + 1, or 4
-// when the ray must be promoted to FP64.
+// when the ray must be promoted to FP64.  kVol builds in the volumetric
+// intensity as a seventh component (Eq. 88; see ray_step64).
+template <bool kVol>
 __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricConsts<float>& mf,
                                            const MxConsts& c,
                                            RayMx& r, const TraceArgs& a, int64_t item,
@@ -324,6 +349,8 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     for (int x = 0; x < 4; ++x) q[u][x] = 0.f;
   bool bad = false;
   float W = 0.f, P2oD = 1.f;
+  const bool vol = kVol && ip.volumetric;
+  float kI = kVol ? r.fI : 0.f, s5I = 0.f, seI = 0.f;
 #pragma unroll 1
   for (int j = 0; j < 7; ++j) {
     // all coefficients, zeros included: branching around the zero terms
@@ -335,6 +362,10 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
       s5[i] = fmaf(bj, k[i], s5[i]);
       se[i] = fmaf(ej, k[i], se[i]);
       sd[i] = fmaf(dj, k[i], sd[i]);
+    }
+    if (kVol) {
+      s5I = fmaf(bj, kI, s5I);
+      seI = fmaf(ej, kI, seI);
     }
     if (j == 6) break;
 #pragma unroll
@@ -348,6 +379,9 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     for (int x = 0; x < 4; ++x) ys[x] = r.yh[kQC(x)] + (r.yl[kQC(x)] + h * q[0][x]);
     bool ok = geo_rhs(mf, r.Ef, r.ellf, ys[0], ys[1], ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
+    // the source depends on the state only, so its stage-input sum is not needed
+    if (vol)
+      kI = vol_source32(ip, mf, r.Ef, r.ellf, ys[0], dtheta_eq(r.yh[2], r.yl[2], h * q[0][1]));
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
 #pragma unroll
@@ -364,7 +398,13 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     float qe = __fdividef(h * se[i], sc);
     err2 += qe * qe;
   }
-  float err = sqrtf(err2 / 6.f);
+  const float dI = h * s5I;
+  if (vol) {
+    const float sc = c.atol + c.rtol * fmaxf(fabsf(r.Ih), fabsf(r.Ih + dI));
+    const float qe = __fdividef(h * seI, sc);
+    err2 += qe * qe;
+  }
+  float err = sqrtf(vol ? err2 / 7.f : err2 / 6.f);
   r.steps++;
   if (bad || !(err <= 1.f)) {
     r.h = bad ? 0.5f * h : h * step_factor(err, true);
@@ -408,6 +448,10 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     r.yl[i] = nl[i];
     r.f[i] = k[i];
   }
+  if (vol) {
+    df_add(r.Ih, r.Il, dI);
+    r.fI = kI;
+  }
   // polar axis (see reflect_axis): theta -> -theta or 2 pi - theta,
   // p_th -> -p_th, phi -> phi + pi
   if (r.yh[2] < 0.f || r.yh[2] > kPiHi) {
@@ -419,6 +463,8 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
       df_from(pth, r.yh[5], r.yl[5]);
       df_from(ph, r.yh[3], r.yl[3]);
       rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f);
+      if (vol)
+        r.fI = vol_source32(ip, mf, r.Ef, r.ellf, r.yh[1], dtheta_eq(r.yh[2], r.yl[2], 0.f));
     }
   }
   float hdv = fabsf(W) / P2oD;
@@ -428,6 +474,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   if (R > c.R_esc) return 1;
   r.h = h * step_factor(err, r.rejected);
   r.rejected = false;
+  if (vol) r.h = layer_cap(ip.vf[0], ip.vf[1], r.yh[1], r.yh[2], r.f[1], r.f[2], r.h);
   // image order n = N_cross - 1 (Sec. 4.2): rays winding to n >= promote_order
   // are promoted
   if (may_promote && (R < c.promote_R || (r.cs.ncross >= c.promote_nc && R < c.demote_R)))
@@ -437,8 +484,9 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
 
 // MinBlocks = 0 leaves the register count to the compiler (3 blocks of 128
 // threads per SM); MinBlocks = 4 caps it at 128 registers for 4 blocks at a
-// small spill cost.  The autotuner picks between them.
-template <int MinBlocks>
+// small spill cost.  The autotuner picks between them.  Vol builds in the
+// volumetric intensity; the thin-disk builds carry none of its registers.
+template <int MinBlocks, bool Vol>
 __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t n_items = pass_items(a);
@@ -470,7 +518,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
           img = s.img;
           ip = &a.ip[img];
           mf = metric_consts<float>(*ip);
-          mx_resume(s, mf, r);
+          mx_resume<Vol>(*ip, s, mf, r);
         } else {
           double X, Y;
           int64_t pix;
@@ -480,7 +528,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
           mf = metric_consts<float>(*ip);
           c.rtol = (float)fmax(ip->rtol, 1e-9);  // FP32 noise floor of the estimate
           c.atol = (float)ip->atol;
-          ray_init_mx(*ip, mf, c, X, Y, r);
+          ray_init_mx<Vol>(*ip, mf, c, X, Y, r);
         }
         c.rtol = (float)fmax(ip->rtol, 1e-9);  // FP32 noise floor of the estimate
         c.atol = (float)ip->atol;
@@ -504,7 +552,9 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
     w_lanes += (unsigned long long)__popc(am);
     if (active) {
       const int acc0 = r.nacc, rej0 = r.nrej;
-      int term = ray_step_mx(*ip, mf, c, r, a, item, img, may_promote);
+      int term = ray_step_mx<Vol>(*ip, mf, c, r, a, item, img, may_promote);
+      // the volumetric integral rides in the float pair until hand-off
+      if (Vol && term && ip->volumetric) r.cs.I[0] = df_to(r.Ih, r.Il);
       w_acc += (unsigned long long)(r.nacc - acc0);
       w_rej += (unsigned long long)(r.nrej - rej0);
       if (term == 4) {
@@ -546,10 +596,16 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
 }
 
 cudaError_t launch_trace_mixed(const TraceArgs& a, LaunchShape s, cudaStream_t st) {
-  if (s.variant == 1)
-    trace_mixed_kernel<4><<<s.blocks, s.threads, 0, st>>>(a);
-  else
-    trace_mixed_kernel<0><<<s.blocks, s.threads, 0, st>>>(a);
+  if (a.any_volumetric) {
+    if (s.variant == 1)
+      trace_mixed_kernel<4, true><<<s.blocks, s.threads, 0, st>>>(a);
+    else
+      trace_mixed_kernel<0, true><<<s.blocks, s.threads, 0, st>>>(a);
+  } else if (s.variant == 1) {
+    trace_mixed_kernel<4, false><<<s.blocks, s.threads, 0, st>>>(a);
+  } else {
+    trace_mixed_kernel<0, false><<<s.blocks, s.threads, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -558,9 +614,9 @@ int trace_default_blocks_per_sm(int precision, int threads, int variant) {
   if (precision == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_fp64_kernel_ptr(variant), threads, 0);
   else if (variant == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel<4>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel<4, false>, threads, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel<0>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_mixed_kernel<0, false>, threads, 0);
   return nb > 0 ? nb : 1;
 }
 
