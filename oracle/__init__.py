@@ -129,6 +129,9 @@ def _load():
         lib.orc_trace_pixels.argtypes = [P, C.c_int64, C.POINTER(C.c_int32), D,
                                          C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
         lib.orc_trace_pixels.restype = C.c_int
+        lib.orc_shadow_boundary.argtypes = [P, C.c_int64, D, C.c_double, C.c_double, C.c_double,
+                                            D, D, C.POINTER(C.c_int32)]
+        lib.orc_shadow_boundary.restype = C.c_int
         lib.orc_trace_points_record.argtypes = [P, C.c_int64, D, C.POINTER(Ray), D, C.c_int,
                                                 C.POINTER(C.c_int32)]
         lib.orc_trace_points_record.restype = C.c_int
@@ -362,6 +365,22 @@ def trace_pixels(P: Problem, ij) -> dict:
     if rc:
         raise ValueError(f"oracle trace_pixels failed (code {rc})")
     return dict(val=val[:n], level=lev[:n], rays=nr[:n])
+
+
+def shadow_boundary(P: Problem, psi, b_lo: float, b_hi: float, tol: float) -> dict:
+    """Shadow boundary along screen directions psi (Sec. 4.1, Eqs. 78-79) by
+    bisection in b; returns the final brackets b_in (captured side), b_out
+    (escaping side) and per-direction flags (1: b_lo not captured, 2: b_hi
+    captured, 4: an undetermined ray was met)."""
+    psi = np.ascontiguousarray(np.asarray(psi, dtype=np.float64).reshape(-1))
+    n = psi.shape[0]
+    b_in, b_out = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    flags = np.zeros(max(n, 1), np.int32)
+    rc = _load().orc_shadow_boundary(C.byref(P), n, _dp(psi), b_lo, b_hi, tol, _dp(b_in),
+                                     _dp(b_out), flags.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc:
+        raise ValueError(f"oracle shadow_boundary failed (code {rc})")
+    return dict(b_in=b_in[:n], b_out=b_out[:n], flags=flags[:n])
 
 
 def _rays_to_numpy(rays, n):

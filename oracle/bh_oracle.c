@@ -1062,3 +1062,52 @@ int orc_geometry(const orc_problem* P, double out4[4]) {
   out4[0] = G.r_plus; out4[1] = G.R_in; out4[2] = G.R_cap; out4[3] = G.R_esc;
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Shadow boundary (Sec. 4.1, Eqs. 78-79): for each polar direction psi of  */
+/* the screen, X = b cos psi and Y = b sin psi, the impact parameter b is   */
+/* varied and the transition between captured and escaping rays located.    */
+/* Reading: plain bisection of [b_lo, b_hi] until the bracket is at most    */
+/* tol wide; "captured" is status 1, and every other fate (escape,          */
+/* undetermined) counts on the escaping side.  Per direction the final      */
+/* bracket is returned (b_in on the captured side, b_out on the escaping    */
+/* side) with flags: 1 if b_lo is not captured, 2 if b_hi is captured (in   */
+/* either case no transition is bracketed and [b_lo, b_hi] is returned),   */
+/* 4 if a traced ray was undetermined.                                      */
+/* ------------------------------------------------------------------------ */
+static int orc_captured(const orc_problem* P, const orc_geom* G, double b, double psi,
+                        int32_t* flag) {
+  orc_ray r;
+  orc_trace_ray(P, G, b * cos(psi), b * sin(psi), &r);
+  if (r.status == 2) *flag |= 4;
+  return r.status == 1;
+}
+
+int orc_shadow_boundary(const orc_problem* P, int64_t n, const double* psi, double b_lo,
+                        double b_hi, double tol, double* b_in, double* b_out, int32_t* flags) {
+  if (!(b_lo >= 0.0 && b_hi > b_lo && tol > 0.0)) return -1;
+  orc_geom G;
+  int rc = orc_geometry_setup(P, &G);
+  if (rc) return rc;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < n; ++k) {
+    int32_t f = 0;
+    double lo = b_lo, hi = b_hi;
+    if (!orc_captured(P, &G, lo, psi[k], &f)) f |= 1;
+    if (orc_captured(P, &G, hi, psi[k], &f)) f |= 2;
+    if (!(f & 3)) {
+      while (hi - lo > tol) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (orc_captured(P, &G, mid, psi[k], &f))
+          lo = mid;
+        else
+          hi = mid;
+      }
+    }
+    b_in[k] = lo;
+    b_out[k] = hi;
+    flags[k] = f;
+  }
+  return 0;
+}
