@@ -108,6 +108,8 @@ def _load():
         lib.orc_extremal_spin.argtypes = [P, D]; lib.orc_extremal_spin.restype = C.c_double
         lib.orc_circular.argtypes = [P, C.c_double, D, D]; lib.orc_circular.restype = C.c_int
         lib.orc_isco.argtypes = [P, D]; lib.orc_isco.restype = C.c_int
+        lib.orc_ergosurface.argtypes = [P, C.c_double, D]
+        lib.orc_ergosurface.restype = C.c_int
         lib.orc_emissivity.argtypes = [P, C.c_double, C.c_double, C.c_double]
         lib.orc_emissivity.restype = C.c_double
         lib.orc_launch.argtypes = [P, C.c_double, C.c_double, D, D, D, D, D]
@@ -237,6 +239,13 @@ def extremal_spin(P: Problem):
     Re = C.c_double(0.0)
     chi_e = _load().orc_extremal_spin(C.byref(P), C.byref(Re))
     return chi_e, Re.value
+
+
+def ergosurface(P: Problem, th: float):
+    """Outer stationary-limit radius R_s(theta) (Eq. 40), or None."""
+    r = C.c_double(0.0)
+    rc = _load().orc_ergosurface(C.byref(P), th, C.byref(r))
+    return None if rc else r.value
 
 
 def circular(P: Problem, R: float):

@@ -1111,3 +1111,32 @@ int orc_shadow_boundary(const orc_problem* P, int64_t n, const double* psi, doub
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Outer stationary-limit surface (Sec. 2.3, Eqs. 38-41): R_s(theta) is the */
+/* largest positive root of R^2 H(R) + chi^2 cos^2 theta = 0 (Eq. 40),      */
+/* found as orc_horizon finds R_+: scan downward from R = 50 in steps of    */
+/* 1e-3 to the first sign change, then bisect.  Returns 0, or 1 if there    */
+/* is no root.                                                               */
+/* ------------------------------------------------------------------------ */
+int orc_ergosurface(const orc_problem* P, double th, double* R_s) {
+  const double c = cos(th), c2 = P->chi * P->chi * c * c;
+  const double step = 1e-3;
+  double hi = 50.0, fhi = hi * hi * orc_H(P, hi) + c2;
+  if (!(fhi > 0.0)) return 1;
+  for (long k = 1;; ++k) {
+    double lo = 50.0 - k * step;
+    if (lo <= 1e-6) return 1;
+    double flo = lo * lo * orc_H(P, lo) + c2;
+    if (flo <= 0.0) {
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (mid * mid * orc_H(P, mid) + c2 > 0.0) hi = mid; else lo = mid;
+      }
+      *R_s = hi;
+      return 0;
+    }
+    hi = lo;
+  }
+}
