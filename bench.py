@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "geodesic rays/s & images/s at 512^2, mixed vs FP64 at <=1e-4 rel intensity err"
 WORKLOAD = ("512x512 sweep: {Einasto lam_E=0.1, cored-NFW eta=0.02 lam_c=10, Kerr} x incl "
             "{17,80} deg, a=0.9, R_o=1000, +-12 M, 4x4 refinement x3 levels, thin disk from r_ISCO")
+WORKLOAD_VOL = WORKLOAD.replace("thin disk from r_ISCO",
+                                "volumetric layer from r_ISCO (Eqs. 83-88, H0=h=0.05)")
 # Algorithmic FP64/FP32 operations per accepted Dormand-Prince step: six
 # right-hand-side evaluations (84 each for the Kerr lapse, counted from the
 # separated Hamilton equations) plus the stage combinations, the 5th-order
@@ -591,6 +593,8 @@ def main():
                     default="sweep512",
                     help="sweep512: the headline line; sweep96 and vis1024: the batched-sweep "
                          "and visibility measurements")
+    ap.add_argument("--emission", choices=["thin", "volumetric"], default="thin",
+                    help="sweep512: thin disk (the headline) or the volumetric layer (Eq. 88)")
     ap.add_argument("--autotune", action="store_true", help="sweep96: autotune the plan first")
     ap.add_argument("--no-autotune", action="store_true",
                     help="sweep512: keep the default launch shapes")
@@ -631,7 +635,8 @@ def main():
         fn = {"sweep96": run_sweep96, "vis1024": run_vis1024,
               "adjoint256": run_adjoint, "kerr64": run_kerr64}[args.workload]
         return fn(args, B, workloads, dev, stream)
-    flats = workloads.sweep_512(precision=prec)
+    vol = args.emission == "volumetric"
+    flats = workloads.sweep_512(precision=prec, volumetric=vol)
     items = [B.from_flat(d) for d in flats]
     plan = B.Plan(items, device=dev, keys_cap=KEYS_CAP)
 
@@ -750,7 +755,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == B.FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "images": len(items), "nx": 512, "ny": 512,
+            "config": {"workload": WORKLOAD_VOL if vol else WORKLOAD, "images": len(items),
+                       "nx": 512, "ny": 512,
                        "levels": 3, "precision": "fp64" if prec == B.FP64 else "mixed",
                        "l2": "working set > L2 (refinement records ~GBs); no flush",
                        "parallelism": f"dp{world}"},

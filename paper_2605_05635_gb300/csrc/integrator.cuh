@@ -175,6 +175,15 @@ __device__ __forceinline__ double emissivity_eq(const ImgParams& ip, double R) {
 // emitter of Eqs. (90)-(91) at the cylindrical radius rho of the equatorial
 // metric (reading); 0 where no timelike circular orbit exists there.  The
 // tapers are written 0.5 (1 + tanh a) = 1 / (1 + exp(-2 a)).
+// 1 / (1 + e^a) without overflow: with t = e^{-|a|} in (0, 1], it is
+// t / (1 + t) for a >= 0 and 1 / (1 + t) otherwise (the tapers of
+// Eqs. 85-86 as logistic functions, 0.5 (1 + tanh x) = 1 / (1 + e^{-2x})).
+__device__ __forceinline__ double logistic_neg(double a) {
+  const double t = d_exp(-fabs(a));
+  const double s = d_rcp(1.0 + t);
+  return a >= 0.0 ? t * s : s;
+}
+
 static __device__ __noinline__ double vol_source64(const ImgParams& ip, MetricConsts<double> m,
                                                    double E, double ell, double R, double th) {
   double s, c;
@@ -184,8 +193,8 @@ static __device__ __noinline__ double vol_source64(const ImgParams& ip, MetricCo
   if (!(rho > 0.0) || !emitter_g(m, rho, E, ell, g)) return 0.0;
   const double Hd = ip.H0 + ip.hh * rho;                        // Eq. (84)
   const double iH = d_rcp(Hd);
-  const double tin = d_rcp(1.0 + d_exp(-2.0 * (rho - ip.R_in) * ip.isig_in));    // Eq. (85)
-  const double tout = d_rcp(1.0 + d_exp(2.0 * (rho - ip.R_out) * ip.isig_out));  // Eq. (86)
+  const double tin = logistic_neg(-2.0 * (rho - ip.R_in) * ip.isig_in);    // Eq. (85)
+  const double tout = logistic_neg(2.0 * (rho - ip.R_out) * ip.isig_out);   // Eq. (86)
   const double lnj = -ip.p * d_log1p(rho * ip.iR_in - 1.0) - (rho - ip.R_in) * ip.iR_s -
                      0.5 * (z * iH) * (z * iH);                 // Eq. (83)
   return g * g * g * ip.j0 * d_exp(lnj) * tin * tout;

@@ -94,6 +94,13 @@ __device__ __forceinline__ float dtheta_eq(float th_h, float th_l, float extra) 
 // theta given as dth = theta - pi/2 (see dtheta_eq), as vol_source64 (mirror
 // point past the polar axis, emitter at the cylindrical radius rho, tapers as
 // logistic functions), from the image's FP32 emission constants.
+// 1 / (1 + e^a) without overflow (see logistic_neg), FP32.
+__device__ __forceinline__ float logistic_neg_f(float a) {
+  const float t = __expf(-fabsf(a));
+  const float s = __fdividef(1.f, 1.f + t);
+  return a >= 0.f ? t * s : s;
+}
+
 static __device__ __noinline__ float vol_source32(const ImgParams& ip, MetricConsts<float> m,
                                                   float E, float ell, float R, float dth) {
   float s, c;
@@ -103,8 +110,8 @@ static __device__ __noinline__ float vol_source32(const ImgParams& ip, MetricCon
   if (!(rho > 0.f) || !emitter_g_f(m, rho, E, ell, g)) return 0.f;
   const float* v = ip.vf;  // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
   const float zH = __fdividef(z, v[0] + v[1] * rho);                    // Eq. (84)
-  const float tin = __fdividef(1.f, 1.f + __expf(-2.f * (rho - v[2]) * v[3]));   // Eq. (85)
-  const float tout = __fdividef(1.f, 1.f + __expf(2.f * (rho - v[5]) * v[4]));   // Eq. (86)
+  const float tin = logistic_neg_f(-2.f * (rho - v[2]) * v[3]);   // Eq. (85)
+  const float tout = logistic_neg_f(2.f * (rho - v[5]) * v[4]);   // Eq. (86)
   const float lnj = -v[6] * __logf(rho * v[9]) - (rho - v[2]) * v[7] - 0.5f * zH * zH;
   return g * g * g * v[8] * __expf(lnj) * tin * tout;                    // Eq. (83)
 }

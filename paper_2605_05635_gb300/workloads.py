@@ -40,15 +40,17 @@ def kerr_64():
                 **FP64_INTEG)
 
 
-def sweep_512(precision=0):
+def sweep_512(precision=0, volumetric=0):
     """Six 512^2 images: {Einasto, cored-NFW, Kerr} x i in {17, 80} deg at
-    a = 0.9, +-12 M, 4x4 refinement to 3 levels."""
+    a = 0.9, +-12 M, 4x4 refinement to 3 levels; thin disk, or with
+    ``volumetric`` the layer of Eqs. 83-88 (H0 = h = 0.05) integrated along
+    the ray."""
     out = []
     for metric in (EINASTO, CNFW, KERR):
         for inc in (17.0, 80.0):
             d = dict(metric=metric, chi=0.9, incl=math.radians(inc), r_obs=1000.0, nx=512,
                      ny=512, x_min=-12.0, x_max=12.0, y_min=-12.0, y_max=12.0, levels=3,
-                     **HALO[metric], **EMISSION,
+                     **HALO[metric], **EMISSION, volumetric=int(volumetric),
                      **(MIXED_INTEG if precision == 1 else FP64_INTEG))
             out.append(d)
     return out

@@ -84,6 +84,17 @@ def test_argument_errors_return_before_device_work(B):
     code = lib.bh_trace_points(C.byref(st), C.byref(incl), C.byref(em), C.byref(it), 0, None,
                                None, ws, 0, None)
     assert code == 1
+    # volumetric emission (Eq. 88): flag in {0, 1}, H0 > 0, h >= 0 and finite
+    for kw in (dict(volumetric=2), dict(volumetric=1, H0=0.0), dict(volumetric=1, h=-1.0),
+               dict(volumetric=1, h=float("inf"))):
+        vem = B.Emission(**kw)._c()
+        code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(vem), C.byref(it), 0,
+                                   None, None, ws, 0, None)
+        assert code == 1, kw
+    vem = B.Emission(volumetric=1)._c()
+    code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(vem), C.byref(it), 0, None,
+                               None, ws, 0, None)
+    assert code == 4   # arguments valid: only the workspace is missing
 
 
 def test_workspace_sizes(B):
