@@ -543,6 +543,107 @@ def run_kerr64(args, B, workloads, dev, stream):
     print(json.dumps(line), flush=True)
 
 
+METRIC_SHADOW = "shadow-boundary points/s (Fig. 5: 3 metrics x 4096 directions, b to 1e-10)"
+WORKLOAD_SHADOW = ("Fig. 5 shadow boundaries: {Kerr, Einasto lam_E=0.3, cored-NFW eta=0.02 "
+                   "lam_c=10} at a=0.5, incl 60 deg, R_o=1000; 4096 directions each, b in "
+                   "[1, 9] bracketed to 1e-10, FP64 rtol 1e-10")
+
+
+def run_shadow(args, B, workloads, dev, stream):
+    """One step brackets the shadow boundary of the three Fig. 5 spacetimes
+    along 4096 screen directions each (three calls on one stream)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    flats, psi, lo, hi, tol = workloads.shadow_fig5()
+    items = [B.from_flat(d) for d in flats]
+    n = len(psi)
+    psi_d = torch.tensor(psi, dtype=torch.float64, device=dev)
+    stats = [torch.zeros(3, dtype=torch.int64, device=dev) for _ in items]
+    res = [None] * len(items)
+
+    def step():
+        for i, (st, cam, _, it) in enumerate(items):
+            res[i] = B.shadow_boundary(st, cam, it, psi_d, lo, hi, tol, device=dev, stream=stream,
+                                       stats=stats[i])
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        ms = _events_ms(stream, step, args.steps)
+        clocks = sampler.stop()
+        counts = np.sum([s.cpu().numpy() for s in stats], axis=0)   # the last step's
+        flags = np.concatenate([r[2].cpu().numpy() for r in res])
+        b_in = [r[0].cpu().numpy() for r in res]
+        b_out = [r[1].cpu().numpy() for r in res]
+        # end to end: directions from pinned host memory, brackets back to the host
+        psi_h = torch.tensor(psi, dtype=torch.float64).pin_memory()
+        host = [torch.empty(n, dtype=torch.float64, pin_memory=True)
+                for _ in range(2 * len(items))]
+        torch.cuda.synchronize(dev)
+        n_e2e = max(1, min(3, args.steps))
+        w0 = time.perf_counter()
+        for _ in range(n_e2e):
+            pd = psi_h.to(dev, non_blocking=True)
+            for i, (st, cam, _, it) in enumerate(items):
+                bi, bo, _ = B.shadow_boundary(st, cam, it, pd, lo, hi, tol, device=dev,
+                                              stream=stream)
+                host[2 * i].copy_(bi, non_blocking=True)
+                host[2 * i + 1].copy_(bo, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        w1 = time.perf_counter()
+    points = len(items) * n
+    value = points / (ms / 1e3)
+    ach = counts[1] * FLOP_PER_STEP / (ms / 1e3) / 1e12
+    # the oracle's bisection on a bounded sample of the same directions
+    oracle.build()
+    rng = np.random.default_rng(7)
+    t_end = time.time() + args.cpu_seconds
+    cpu_pts, cpu_t, worst = 0, 0.0, 0.0
+    while time.time() < t_end:
+        for i, d in enumerate(flats):
+            k = rng.choice(n, 8, replace=False)
+            P = oracle.problem(**{kk: v for kk, v in d.items() if kk in oracle.DEFAULTS})
+            t0 = time.perf_counter()
+            r = oracle.shadow_boundary(P, np.asarray(psi)[k], lo, hi, tol)
+            cpu_t += time.perf_counter() - t0
+            cpu_pts += len(k)
+            mid_o = 0.5 * (r["b_in"] + r["b_out"])
+            mid_g = 0.5 * (b_in[i][k] + b_out[i][k])
+            worst = max(worst, float(np.max(np.abs(mid_g - mid_o))))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "metric": METRIC_SHADOW, "value": value, "unit": "boundary points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_SHADOW, "directions": n, "spacetimes": len(items),
+                   "l2": "ALU-bound, ray state in registers, 32 KB of inputs; no flush",
+                   "parallelism": "dp1"},
+        "rays_per_step": int(counts[0]), "rays_per_s": counts[0] / (ms / 1e3),
+        "accepted_steps_per_step": int(counts[1]),
+        "flags_nonzero": int(np.count_nonzero(flags)),
+        "max_abs_b_diff_vs_oracle_sample": worst,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_FLOPS / 1e12,
+                     "unit": "TFLOP/s", "frac": ach * 1e12 / FP64_PEAK_FLOPS, "traffic": None,
+                     "kernel": "shadow_kernel", "flop_per_accepted_step": FLOP_PER_STEP,
+                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
+        "cpu_baseline": {"value": cpu_pts / cpu_t, "unit": "boundary points/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{cpu_pts} random directions of the same three spacetimes "
+                                   f"(bisection, 8 per spacetime per round), {cpu_t:.1f} s"},
+        "clocks": clocks,
+        "e2e": {"value": n_e2e * points / (w1 - w0), "unit": "boundary points/s",
+                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": 2 * points * 8},
+        "gpu_launches": len(items) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _measured_peak(key):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -589,7 +690,8 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
-    ap.add_argument("--workload", choices=["sweep512", "sweep96", "vis1024", "adjoint256", "kerr64"],
+    ap.add_argument("--workload", choices=["sweep512", "sweep96", "vis1024", "adjoint256", "kerr64",
+                                           "shadow"],
                     default="sweep512",
                     help="sweep512: the headline line; sweep96 and vis1024: the batched-sweep "
                          "and visibility measurements")
@@ -633,7 +735,8 @@ def main():
         if world > 1:
             raise SystemExit(f"--workload {args.workload} runs on one GPU")
         fn = {"sweep96": run_sweep96, "vis1024": run_vis1024,
-              "adjoint256": run_adjoint, "kerr64": run_kerr64}[args.workload]
+              "adjoint256": run_adjoint, "kerr64": run_kerr64,
+              "shadow": run_shadow}[args.workload]
         return fn(args, B, workloads, dev, stream)
     vol = args.emission == "volumetric"
     flats = workloads.sweep_512(precision=prec, volumetric=vol)

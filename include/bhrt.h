@@ -16,7 +16,9 @@
  *     with transfer maps R_em, phi_em, T_em (Eq. 82);
  *   - redshift g (Eq. 89) for circular emitters (Eqs. 90-91) and the
  *     semi-analytic emissivity (Eqs. 83-87), thin-disk intensity
- *     sum over crossings of g^3 j (reading of Eq. 88);
+ *     sum over crossings of g^3 j (reading of Eq. 88), or the
+ *     finite-thickness integral of Eq. (88) along the ray;
+ *   - the shadow boundary along screen directions (Sec. 4.1, Eqs. 78-79);
  *   - adaptive refinement of the screen near class boundaries
  *     (Introduction and Sec. 4; the rule is a documented reading);
  *   - image diagnostics (Sec. 6.2-6.3, Eqs. 92-107) and visibilities
@@ -208,6 +210,34 @@ bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh
                           const bh_integrator* integ, int64_t n, const double* xy,
                           bh_ray_record* records, void* workspace, size_t workspace_bytes,
                           void* stream);
+
+/* Shadow boundary (Sec. 4.1, Eqs. 78-79).  Along each screen direction
+ * psi[k] (device doubles, radians), X = b cos psi, Y = b sin psi, the
+ * transition between captured and escaping rays is bracketed in the impact
+ * parameter b inside [b_lo, b_hi]: on return (stream-ordered, device
+ * outputs) b_in[k] <= b_out[k] with the ray at b_in[k] captured, the ray at
+ * b_out[k] not captured (escaped or undetermined) and b_out[k] - b_in[k] <=
+ * b_tol, unless flagged.  flags[k]: 1 the ray at b_lo is not captured, 2 the
+ * ray at b_hi is captured (with 1 or 2 no transition is bracketed and
+ * [b_lo, b_hi] is returned), 4 some traced ray was undetermined, 8 the
+ * integrator's time budget ran out first (bracket as far as it got; the
+ * workspace status is then BH_ERR_TIMEOUT).  A bracket whose width can no
+ * longer shrink in FP64 stops there.  If the fate is not monotone in b along
+ * a direction, the transition nearest to b_lo among those the samples see
+ * is returned.  Rays are traced by the FP64 integrator (integ->precision
+ * must be 0) with the tolerances, step limit and thresholds of integ; the
+ * camera gives R_o and the inclination (its screen extent and pixel counts
+ * are not used); emission plays no part.  Requires 0 <= b_lo < b_hi,
+ * b_tol > 0, all finite (else BH_ERR_INVALID_ARG).  stats (optional device
+ * int64[3], may be NULL) receives the rays traced and their accepted and
+ * rejected Dormand-Prince steps.  Needs bh_shadow_workspace_size(n_psi)
+ * bytes of 256-byte aligned workspace. */
+bh_status bh_shadow_workspace_size(int64_t n_psi, size_t* bytes);
+bh_status bh_shadow_boundary(const bh_spacetime* st, const bh_camera* cam,
+                             const bh_integrator* integ, int64_t n_psi, const double* psi,
+                             double b_lo, double b_hi, double b_tol, double* b_in, double* b_out,
+                             int32_t* flags, int64_t* stats, void* workspace,
+                             size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Plans: a batch whose per-image constants are computed and uploaded once,

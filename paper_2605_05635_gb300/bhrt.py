@@ -229,6 +229,11 @@ def lib():
                                       C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                       C.c_void_p]
         L.bh_workspace_status.argtypes = [C.c_void_p, C.c_void_p]
+        L.bh_shadow_workspace_size.argtypes = [C.c_int64, P(C.c_size_t)]
+        L.bh_shadow_boundary.argtypes = [P(_Spacetime), P(_Camera), P(_Integrator), C.c_int64,
+                                         C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_size_t, C.c_void_p]
         L.bh_plan_create.argtypes = [C.c_int32, P(_Spacetime), P(_Camera), P(_Emission),
                                      P(_Integrator), P(_ImageOut), C.c_void_p, C.c_size_t,
                                      C.c_void_p, P(C.c_void_p)]
@@ -259,6 +264,7 @@ def lib():
             getattr(L, fn).restype = C.c_int
         for fn in ("bh_host_geometry", "bh_workspace_size", "bh_trace_image", "bh_trace_batch",
                    "bh_points_workspace_size", "bh_trace_points", "bh_workspace_status",
+                   "bh_shadow_workspace_size", "bh_shadow_boundary",
                    "bh_plan_create", "bh_plan_launch", "bh_plan_set_timing", "bh_plan_set_launch",
                    "bh_plan_stats",
                    "bh_plan_destroy"):
@@ -400,6 +406,35 @@ def trace_points(st: Spacetime, cam: Camera, em: Emission, integ: Integrator, xy
                    ((f, np.float64, (3,)) if hasattr(t, "_length_") else (f, np.float64))
                    for f, t in RayRecord._fields_])
     return np.frombuffer(raw, dtype=dt, count=n).copy()
+
+
+def shadow_boundary(st: Spacetime, cam: Camera, integ: Integrator, psi, b_lo: float,
+                    b_hi: float, b_tol: float, device=None, stream=None, stats=None):
+    """Shadow boundary along screen directions ``psi`` (Sec. 4.1, Eqs. 78-79):
+    returns device tensors (b_in, b_out, flags) per direction, the final
+    bracket of the capture / escape transition in the impact parameter and
+    its flags (1 b_lo not captured, 2 b_hi captured, 4 an undetermined ray,
+    8 time budget).  ``stats``, an optional int64 device tensor of 3,
+    receives the rays traced and their accepted and rejected steps."""
+    device = _need_cuda(device)
+    psi_t = torch.as_tensor(psi, dtype=torch.float64).reshape(-1).contiguous().to(device)
+    n = psi_t.shape[0]
+    b_in = torch.empty(max(n, 1), dtype=torch.float64, device=device)
+    b_out = torch.empty_like(b_in)
+    flags = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+    nb = C.c_size_t(0)
+    _check(lib().bh_shadow_workspace_size(n, C.byref(nb)), "bh_shadow_workspace_size")
+    ws = _aligned_workspace(nb.value, device)
+    sp = _stream_ptr(stream)
+    code = lib().bh_shadow_boundary(C.byref(st._c()), C.byref(cam._c()), C.byref(integ._c()), n,
+                                    C.c_void_p(psi_t.data_ptr()), b_lo, b_hi, b_tol,
+                                    C.c_void_p(b_in.data_ptr()), C.c_void_p(b_out.data_ptr()),
+                                    C.c_void_p(flags.data_ptr()),
+                                    C.c_void_p(stats.data_ptr() if stats is not None else 0),
+                                    C.c_void_p(ws.data_ptr()), ws.numel(), sp)
+    _check(code, "bh_shadow_boundary")
+    _check(lib().bh_workspace_status(C.c_void_p(ws.data_ptr()), sp), "device status")
+    return b_in[:n], b_out[:n], flags[:n]
 
 
 class Plan:

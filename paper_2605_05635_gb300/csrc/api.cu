@@ -352,14 +352,14 @@ Caps default_caps(int n, const bh_camera& c) {
   return k;
 }
 
-int num_sms() {
+}  // namespace
+
+int bhrt::num_sms() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return sms > 0 ? sms : 1;
 }
-
-}  // namespace
 
 // ------------------------------------------------------------------- plan
 struct bh_plan_s {
@@ -704,6 +704,86 @@ bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh
   LaunchShape sh{num_sms() * trace_default_blocks_per_sm(integ->precision, 128), 128};
   cudaError_t e = integ->precision == 0 ? launch_trace_fp64(a, sh, cs) : launch_trace_mixed(a, sh, cs);
   return e == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+}
+
+bh_status bh_shadow_workspace_size(int64_t n_psi, size_t* bytes) {
+  if (n_psi < 0 || !bytes) return BH_ERR_INVALID_ARG;
+  *bytes = align256(sizeof(WsHeader)) + align256(sizeof(ImgParams));
+  return BH_OK;
+}
+
+bh_status bh_shadow_boundary(const bh_spacetime* st, const bh_camera* cam,
+                             const bh_integrator* integ, int64_t n_psi, const double* psi,
+                             double b_lo, double b_hi, double b_tol, double* b_in, double* b_out,
+                             int32_t* flags, int64_t* stats, void* workspace,
+                             size_t workspace_bytes, void* stream) {
+  if (!st || !cam || !integ || n_psi < 0 || (n_psi > 0 && (!psi || !b_in || !b_out || !flags)))
+    return BH_ERR_INVALID_ARG;
+  if (!(std::isfinite(b_lo) && std::isfinite(b_hi) && b_lo >= 0.0 && b_hi > b_lo &&
+        b_tol > 0.0 && std::isfinite(b_tol)))
+    return BH_ERR_INVALID_ARG;
+  if (integ->precision != 0) return BH_ERR_INVALID_ARG;  // FP64 integrator only
+  // the screen's extent and pixel counts play no part: a one-pixel screen;
+  // no emission enters a ray's fate: the thin disk with R_in = R_+ + dR_in
+  bh_camera c = *cam;
+  c.nx = c.ny = 1;
+  c.x_min = c.y_min = -1.0;
+  c.x_max = c.y_max = 1.0;
+  c.refine_levels = 0;
+  c.refine_capacity = 0;
+  bh_emission e{};
+  e.r_in_mode = 1;
+  e.j0 = 1.0;
+  e.p = 2.0;
+  e.R_s = 8.0;
+  e.sigma_in = 0.2;
+  e.sigma_out = 2.0;
+  e.R_out = 20.0;
+  e.dR_in = 0.5;
+  e.H0 = 0.05;
+  e.h = 0.05;
+  ImgParams ip;
+  bh_status s = make_params(*st, c, e, *integ, ip);
+  if (s != BH_OK) return s;
+  size_t need;
+  bh_shadow_workspace_size(n_psi, &need);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
+    return BH_ERR_WORKSPACE;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  ImgParams* dip = reinterpret_cast<ImgParams*>(ws + align256(sizeof(WsHeader)));
+  if (cudaMemcpyAsync(dip, &ip, sizeof(ip), cudaMemcpyHostToDevice, cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  if (launch_begin(hdr, (unsigned long long)(integ->time_budget_s * 1e9), cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  if (stats && cudaMemsetAsync(stats, 0, 3 * sizeof(int64_t), cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  if (n_psi == 0) return BH_OK;
+  // lanes per direction: the largest power of two <= 32 with directions x
+  // lanes within the resident threads (bisection when the directions alone
+  // fill the GPU); a grid of whole warps covering every group once, at most
+  // one resident wave
+  const int64_t resident = shadow_resident_threads();
+  int G = 1;
+  while (G < 32 && n_psi * (int64_t)(2 * G) <= resident) G *= 2;
+  const int64_t warps = (n_psi * G + 31) / 32;
+  const int64_t max_blocks = resident / 128;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 3) / 4, max_blocks));
+  ShadowArgs a{};
+  a.hdr = hdr;
+  a.ip = dip;
+  a.psi = psi;
+  a.n = n_psi;
+  a.b_lo = b_lo;
+  a.b_hi = b_hi;
+  a.tol = b_tol;
+  a.b_in = b_in;
+  a.b_out = b_out;
+  a.flags = flags;
+  a.stats = reinterpret_cast<unsigned long long*>(stats);
+  a.group = G;
+  return launch_shadow(a, blocks, cs) == cudaSuccess ? BH_OK : BH_ERR_CUDA;
 }
 
 bh_status bh_plan_create(int32_t n, const bh_spacetime* st, const bh_camera* cam,

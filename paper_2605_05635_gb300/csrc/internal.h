@@ -92,5 +92,23 @@ cudaError_t launch_mark_expand(const RefineArgs& a, int level, int blocks, cudaS
 cudaError_t launch_assemble(const RefineArgs& a, int level, int blocks, cudaStream_t st);
 cudaError_t launch_write_keys(const RefineArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_begin(WsHeader* hdr, unsigned long long budget_ns, cudaStream_t st);
+int num_sms();
+
+// shadow.cu -- shadow-boundary search (Sec. 4.1, Eqs. 78-79)
+constexpr int kShadowMaxRounds = 200;
+struct ShadowArgs {
+  WsHeader* hdr;
+  const ImgParams* ip;
+  const double* psi;     // [n] screen directions
+  int64_t n;
+  double b_lo, b_hi, tol;
+  double* b_in;          // [n] captured end of the final bracket
+  double* b_out;         // [n] escaping end
+  int32_t* flags;        // [n]
+  unsigned long long* stats;  // optional [3]: rays, accepted, rejected steps
+  int group;             // lanes per direction (1, 2, 4, 8, 16, 32)
+};
+cudaError_t launch_shadow(const ShadowArgs& a, int blocks, cudaStream_t st);
+int shadow_resident_threads();
 
 }  // namespace bhrt

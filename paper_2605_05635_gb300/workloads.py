@@ -56,6 +56,20 @@ def sweep_512(precision=0, volumetric=0):
     return out
 
 
+def shadow_fig5(n_psi=4096):
+    """Shadow boundaries of Fig. 5: Kerr, Einasto (lambda_E = 0.3) and
+    cored-NFW (eta = 0.02, lambda_c = 10) at a = 0.5, i = 60 deg, R_o = 1000,
+    n_psi directions uniform in [0, 2 pi), b bracketed in [1, 9] to 1e-10,
+    FP64 at rtol 1e-10.  Returns (flats, psi, b_lo, b_hi, b_tol)."""
+    flats = [dict(metric=m, chi=0.5, incl=math.radians(60.0), r_obs=1000.0, nx=1, ny=1,
+                  x_min=-1.0, x_max=1.0, y_min=-1.0, y_max=1.0, levels=0, **EMISSION,
+                  **FP64_INTEG, **h)
+             for m, h in ((KERR, {}), (EINASTO, dict(lam_E=0.3)),
+                          (CNFW, dict(eta=0.02, lam_c=10.0)))]
+    psi = [2.0 * math.pi * k / n_psi for k in range(n_psi)]
+    return flats, psi, 1.0, 9.0, 1e-10
+
+
 def sweep_96(seed=20260513, n=256):
     """96 images: 3 metrics x 8 spins x 4 inclinations, n^2 over +-12 M with
     refinement; halo parameters jittered x U(0.8, 1.2) in image order

@@ -95,6 +95,17 @@ def test_argument_errors_return_before_device_work(B):
     code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(vem), C.byref(it), 0, None,
                                None, ws, 0, None)
     assert code == 4   # arguments valid: only the workspace is missing
+    # shadow boundary (Sec. 4.1): bracket, precision, spacetime, workspace
+    def shadow(s, c, i, lo, hi, tol):
+        return lib.bh_shadow_boundary(C.byref(s), C.byref(c), C.byref(i), 0, None, lo, hi, tol,
+                                      None, None, None, None, ws, 0, None)
+    for lo, hi, tol in ((3.0, 2.0, 1e-6), (-1.0, 2.0, 1e-6), (1.0, 2.0, 0.0),
+                        (1.0, float("nan"), 1e-6), (1.0, 2.0, float("inf"))):
+        assert shadow(st, cam, it, lo, hi, tol) == 1
+    assert shadow(st, cam, B.Integrator(precision=1)._c(), 1.0, 9.0, 1e-6) == 1
+    assert shadow(bad, cam, it, 1.0, 9.0, 1e-6) == 2
+    assert shadow(st, far, it, 1.0, 9.0, 1e-6) == 3
+    assert shadow(st, cam, it, 1.0, 9.0, 1e-6) == 4
 
 
 def test_workspace_sizes(B):
