@@ -644,6 +644,109 @@ def run_shadow(args, B, workloads, dev, stream):
     print(json.dumps(line), flush=True)
 
 
+METRIC_SCAN = "spacetimes classified/s (Figs. 3-4 grids: horizon, extremal spin, 16-angle R_s)"
+WORKLOAD_SCAN = ("Einasto (chi, lambda_E) in [0,1.2]x[0.05,1] and cored-NFW (chi, eta) in "
+                 "[0,1.2]x[0,0.3] at lambda_c=10, 1024^2 each; R_+, chi_e, R_e and R_s at 16 "
+                 "polar angles in [0, pi/2]")
+# Hand count of FP64 operations per lapse evaluation R^2 H(R) in the scan
+# (exp by reduction and a degree-13 polynomial, log1p by its atanh series,
+# reciprocals by two Newton steps): Einasto 42, cored-NFW 66; the bench grid
+# is half of each.
+SCAN_FLOP_PER_EVAL = 54
+
+
+def run_scan(args, B, workloads, dev, stream):
+    """One step classifies the two Figs. 3-4 parameter grids (2 x 1024^2
+    spacetimes) in one bh_geometry_scan call."""
+    import numpy as np
+    import torch
+
+    import oracle
+    metric, chi, lam_E, eta, lam_c, theta = workloads.geometry_grid()
+    n = metric.shape[0]
+    rec = np.zeros(n, dtype=np.dtype([("metric", "<i4"), ("reserved", "<i4"), ("chi", "<f8"),
+                                      ("lambda_E", "<f8"), ("eta", "<f8"),
+                                      ("lambda_c", "<f8")]))
+    rec["metric"], rec["chi"], rec["lambda_E"], rec["eta"], rec["lambda_c"] = (
+        metric, chi, lam_E, eta, lam_c)
+    raw = rec.view(np.uint8)
+    st_d = torch.from_numpy(raw.copy()).to(dev)
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    res = {}
+
+    def step():
+        res.update(B.geometry_scan(st_d, theta, device=dev, stream=stream, stats=stats))
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        ms = _events_ms(stream, step, args.steps)
+        clocks = sampler.stop()
+        evals = int(stats.sum())                     # the last step's
+        out = {k: v.cpu().numpy() for k, v in res.items()}
+        # end to end: parameters from pinned host memory, results back
+        host_in = torch.from_numpy(raw.copy()).pin_memory()
+        torch.cuda.synchronize(dev)
+        n_e2e = max(1, min(3, args.steps))
+        w0 = time.perf_counter()
+        for _ in range(n_e2e):
+            r = B.geometry_scan(host_in.to(dev, non_blocking=True), theta, device=dev,
+                                stream=stream)
+            {k: v.to("cpu", non_blocking=True) for k, v in r.items()}
+            torch.cuda.synchronize(dev)
+        w1 = time.perf_counter()
+    value = n / (ms / 1e3)
+    ach = evals * SCAN_FLOP_PER_EVAL / (ms / 1e3) / 1e12
+    # the oracle (plain C scans at its own 1e-3 / 1e-4 grids) on a bounded sample
+    oracle.build()
+    rng = np.random.default_rng(11)
+    t_end = time.time() + args.cpu_seconds
+    cpu_n, cpu_t, worst = 0, 0.0, 0.0
+    while time.time() < t_end:
+        i = int(rng.integers(0, n))
+        P = oracle.problem(metric=int(metric[i]), chi=float(chi[i]), lam_E=float(lam_E[i]),
+                           eta=float(eta[i]), lam_c=float(lam_c[i]))
+        t0 = time.perf_counter()
+        ce, _ = oracle.extremal_spin(P)
+        rp = oracle.horizon(P)
+        rs = [oracle.ergosurface(P, float(t)) for t in theta]
+        cpu_t += time.perf_counter() - t0
+        cpu_n += 1
+        worst = max(worst, abs(out["chi_e"][i] - ce) / max(ce, 1e-300))
+        if rp is not None and abs(chi[i]) < ce - 1e-3:
+            worst = max(worst, abs(out["r_plus"][i] - rp) / rp)
+    line = {
+        "metric": METRIC_SCAN, "value": value, "unit": "spacetimes/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_SCAN, "spacetimes": n, "angles": len(theta),
+                   "l2": "ALU-bound; 84 MB of parameters read once per step, no flush",
+                   "parallelism": "dp1"},
+        "lapse_evaluations_per_step": evals,
+        "black_holes": int(np.count_nonzero(out["flags"] == 0)),
+        "max_rel_diff_vs_oracle_sample": worst,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_FLOPS / 1e12,
+                     "unit": "TFLOP/s", "frac": ach * 1e12 / FP64_PEAK_FLOPS, "traffic": None,
+                     "kernel": "scan_horizon_kernel + scan_ergo_kernel",
+                     "flop_per_lapse_evaluation": SCAN_FLOP_PER_EVAL,
+                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
+        "cpu_baseline": {"value": cpu_n / cpu_t, "unit": "spacetimes/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{cpu_n} random grid points, one at a time (the oracle's "
+                                   f"scans are serial), {cpu_t:.1f} s"},
+        "clocks": clocks,
+        "e2e": {"value": n_e2e * n / (w1 - w0), "unit": "spacetimes/s",
+                "h2d_bytes_per_step": int(raw.nbytes),
+                "d2h_bytes_per_step": int(n * (3 * 8 + 4 + 8 * len(theta)))},
+        "gpu_launches": 2 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _measured_peak(key):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -691,7 +794,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--workload", choices=["sweep512", "sweep96", "vis1024", "adjoint256", "kerr64",
-                                           "shadow"],
+                                           "shadow", "scan"],
                     default="sweep512",
                     help="sweep512: the headline line; sweep96 and vis1024: the batched-sweep "
                          "and visibility measurements")
@@ -736,7 +839,7 @@ def main():
             raise SystemExit(f"--workload {args.workload} runs on one GPU")
         fn = {"sweep96": run_sweep96, "vis1024": run_vis1024,
               "adjoint256": run_adjoint, "kerr64": run_kerr64,
-              "shadow": run_shadow}[args.workload]
+              "shadow": run_shadow, "scan": run_scan}[args.workload]
         return fn(args, B, workloads, dev, stream)
     vol = args.emission == "volumetric"
     flats = workloads.sweep_512(precision=prec, volumetric=vol)

@@ -9,7 +9,8 @@
  *     Sigma, F, Delta of Eqs. (23)-(25) and the Boyer-Lindquist components
  *     of Eqs. (27)-(31);
  *   - outer horizon R_+ = largest root of Delta (Eq. 33), extremal spin
- *     Eqs. (34)-(37);
+ *     Eqs. (34)-(37), stationary-limit surface (Eqs. 38-41), also as
+ *     parameter scans over many spacetimes;
  *   - backward null geodesics from a ZAMO screen (Sec. 3.2, Eqs. 63-74),
  *     integrated as Hamilton's equations (Sec. 3.1, Eqs. 46-62);
  *   - capture / escape (Eq. 75) and equatorial crossings (Sec. 3.3, 4.2)
@@ -210,6 +211,25 @@ bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh
                           const bh_integrator* integ, int64_t n, const double* xy,
                           bh_ray_record* records, void* workspace, size_t workspace_bytes,
                           void* stream);
+
+/* Horizon, extremal-spin and stationary-limit scans (Sec. 2.3, Eqs. 33-41):
+ * the parameter-space classification of Figs. 2-4 for n spacetimes st[i]
+ * (DEVICE array of structs, any mix of families), one thread each.  Per
+ * spacetime: R_e[i], the extremal radius (the maximiser of -R^2 H(R) on
+ * (0, 50], where Eq. 36 holds), chi_e[i] = sqrt(-R_e^2 H(R_e)) (Eq. 37, 0 if
+ * -R^2 H never becomes positive), r_plus[i] = R_+, the largest root of
+ * Delta = R^2 H + chi^2 below R = 50 (Eq. 33; 0 if none), and for each of the
+ * n_theta polar angles theta[k] (device, radians) the outer stationary-limit
+ * radius R_s[i*n_theta + k], the largest root of R^2 H + chi^2 cos^2 theta
+ * (Eq. 40; 0 if none; R_s may be NULL when n_theta is 0).  flags[i]: 0 black
+ * hole, 1 no horizon (|chi| > chi_e), 2 invalid parameters (unknown metric,
+ * lambda_E <= 0, lambda_c <= 0, eta < 0 or a non-finite value; outputs 0).
+ * stats (optional device int64[2], may be NULL) receives the lapse
+ * evaluations H(R) of the horizon and of the stationary-limit searches.
+ * All arrays are device arrays; no workspace; asynchronous on stream. */
+bh_status bh_geometry_scan(int64_t n, const bh_spacetime* st, int32_t n_theta,
+                           const double* theta, double* r_plus, double* chi_e, double* R_e,
+                           double* R_s, int32_t* flags, int64_t* stats, void* stream);
 
 /* Shadow boundary (Sec. 4.1, Eqs. 78-79).  Along each screen direction
  * psi[k] (device doubles, radians), X = b cos psi, Y = b sin psi, the

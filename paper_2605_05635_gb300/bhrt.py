@@ -229,6 +229,9 @@ def lib():
                                       C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                       C.c_void_p]
         L.bh_workspace_status.argtypes = [C.c_void_p, C.c_void_p]
+        L.bh_geometry_scan.argtypes = [C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
         L.bh_shadow_workspace_size.argtypes = [C.c_int64, P(C.c_size_t)]
         L.bh_shadow_boundary.argtypes = [P(_Spacetime), P(_Camera), P(_Integrator), C.c_int64,
                                          C.c_void_p, C.c_double, C.c_double, C.c_double,
@@ -264,7 +267,7 @@ def lib():
             getattr(L, fn).restype = C.c_int
         for fn in ("bh_host_geometry", "bh_workspace_size", "bh_trace_image", "bh_trace_batch",
                    "bh_points_workspace_size", "bh_trace_points", "bh_workspace_status",
-                   "bh_shadow_workspace_size", "bh_shadow_boundary",
+                   "bh_shadow_workspace_size", "bh_shadow_boundary", "bh_geometry_scan",
                    "bh_plan_create", "bh_plan_launch", "bh_plan_set_timing", "bh_plan_set_launch",
                    "bh_plan_stats",
                    "bh_plan_destroy"):
@@ -406,6 +409,53 @@ def trace_points(st: Spacetime, cam: Camera, em: Emission, integ: Integrator, xy
                    ((f, np.float64, (3,)) if hasattr(t, "_length_") else (f, np.float64))
                    for f, t in RayRecord._fields_])
     return np.frombuffer(raw, dtype=dt, count=n).copy()
+
+
+def spacetime_array(spacetimes: Sequence[Spacetime], device=None) -> torch.Tensor:
+    """The bh_spacetime structs of ``spacetimes`` as one device byte tensor
+    (the layout bh_geometry_scan reads)."""
+    import numpy as np
+
+    device = _need_cuda(device)
+    arr = (_Spacetime * max(len(spacetimes), 1))(*[s._c() for s in spacetimes])
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8)[: len(spacetimes) * C.sizeof(_Spacetime)]
+    return torch.from_numpy(raw.copy()).to(device)
+
+
+def geometry_scan(spacetimes, theta=(), device=None, stream=None, stats=None):
+    """Horizon, extremal spin and stationary-limit radii of many spacetimes
+    (Sec. 2.3, Eqs. 33-41).  ``spacetimes`` is a sequence of Spacetime or a
+    device tensor from spacetime_array.  Returns device tensors r_plus,
+    chi_e, R_e [n], R_s [n, len(theta)] and flags [n] (0 black hole, 1 no
+    horizon, 2 invalid parameters).  ``stats``, an optional int64 device
+    tensor of 2, receives the lapse evaluations of the two searches."""
+    device = _need_cuda(device)
+    if isinstance(spacetimes, torch.Tensor):
+        st_d = spacetimes
+        n = st_d.numel() // C.sizeof(_Spacetime)
+    else:
+        n = len(spacetimes)
+        st_d = spacetime_array(spacetimes, device)
+    th = torch.as_tensor(theta, dtype=torch.float64).reshape(-1).contiguous().to(device)
+    k = th.shape[0]
+    out = {name: torch.empty(max(n, 1), dtype=torch.float64, device=device)
+           for name in ("r_plus", "chi_e", "R_e")}
+    R_s = torch.empty((max(n, 1), max(k, 1)), dtype=torch.float64, device=device)
+    flags = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+    code = lib().bh_geometry_scan(n, C.c_void_p(st_d.data_ptr() if n else 0), k,
+                                  C.c_void_p(th.data_ptr() if k else 0),
+                                  C.c_void_p(out["r_plus"].data_ptr()),
+                                  C.c_void_p(out["chi_e"].data_ptr()),
+                                  C.c_void_p(out["R_e"].data_ptr()),
+                                  C.c_void_p(R_s.data_ptr() if k else 0),
+                                  C.c_void_p(flags.data_ptr()),
+                                  C.c_void_p(stats.data_ptr() if stats is not None else 0),
+                                  _stream_ptr(stream))
+    _check(code, "bh_geometry_scan")
+    res = {name: v[:n] for name, v in out.items()}
+    res["R_s"] = R_s[:n, :k]
+    res["flags"] = flags[:n]
+    return res
 
 
 def shadow_boundary(st: Spacetime, cam: Camera, integ: Integrator, psi, b_lo: float,

@@ -706,6 +706,29 @@ bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh
   return e == cudaSuccess ? BH_OK : BH_ERR_CUDA;
 }
 
+bh_status bh_geometry_scan(int64_t n, const bh_spacetime* st, int32_t n_theta,
+                           const double* theta, double* r_plus, double* chi_e, double* R_e,
+                           double* R_s, int32_t* flags, int64_t* stats, void* stream) {
+  if (n < 0 || n_theta < 0 || (n > 0 && (!st || !r_plus || !chi_e || !R_e || !flags)) ||
+      (n > 0 && n_theta > 0 && (!theta || !R_s)))
+    return BH_ERR_INVALID_ARG;
+  ScanArgs a{};
+  a.st = st;
+  a.n = n;
+  a.n_theta = n_theta;
+  a.theta = theta;
+  a.r_plus = r_plus;
+  a.chi_e = chi_e;
+  a.R_e = R_e;
+  a.R_s = R_s;
+  a.flags = flags;
+  a.stats = reinterpret_cast<unsigned long long*>(stats);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (stats && cudaMemsetAsync(stats, 0, 2 * sizeof(int64_t), cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  return launch_scan(a, cs) == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+}
+
 bh_status bh_shadow_workspace_size(int64_t n_psi, size_t* bytes) {
   if (n_psi < 0 || !bytes) return BH_ERR_INVALID_ARG;
   *bytes = align256(sizeof(WsHeader)) + align256(sizeof(ImgParams));

@@ -111,4 +111,20 @@ struct ShadowArgs {
 cudaError_t launch_shadow(const ShadowArgs& a, int blocks, cudaStream_t st);
 int shadow_resident_threads();
 
+// scan.cu -- horizon, extremal-spin and stationary-limit scans (Sec. 2.3)
+struct ScanArgs {
+  const bh_spacetime* st;  // [n] device
+  int64_t n;
+  int32_t n_theta;
+  const double* theta;     // [n_theta] device
+  double* r_plus;          // [n]
+  double* chi_e;           // [n]
+  double* R_e;             // [n]
+  double* R_s;             // optional [n][n_theta]
+  int32_t* flags;          // [n]
+  unsigned long long* stats;  // optional [2]: lapse evaluations of the horizon
+                              // and of the stationary-limit kernel
+};
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
+
 }  // namespace bhrt

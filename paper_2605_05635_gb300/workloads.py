@@ -70,6 +70,23 @@ def shadow_fig5(n_psi=4096):
     return flats, psi, 1.0, 9.0, 1e-10
 
 
+def geometry_grid(n=1024, n_theta=16):
+    """Parameter grids of Figs. 3-4: Einasto (chi, lambda_E) over [0, 1.2] x
+    [0.05, 1] and cored-NFW (chi, eta) over [0, 1.2] x [0, 0.3] at
+    lambda_c = 10, n x n each (chi slowest), and n_theta polar angles in
+    [0, pi/2] for the stationary-limit surface.  Returns numpy arrays
+    (metric, chi, lambda_E, eta, lambda_c) of length 2 n^2 and theta."""
+    import numpy as np
+    chi = np.repeat(np.linspace(0.0, 1.2, n), n)
+    u = np.tile(np.linspace(0.0, 1.0, n), n)
+    metric = np.concatenate([np.full(n * n, EINASTO), np.full(n * n, CNFW)]).astype(np.int32)
+    lam_E = np.concatenate([0.05 + 0.95 * u, np.full(n * n, 0.1)])
+    eta = np.concatenate([np.full(n * n, 0.02), 0.3 * u])
+    lam_c = np.full(2 * n * n, 10.0)
+    theta = np.linspace(0.0, 0.5 * math.pi, n_theta)
+    return metric, np.concatenate([chi, chi]), lam_E, eta, lam_c, theta
+
+
 def sweep_96(seed=20260513, n=256):
     """96 images: 3 metrics x 8 spins x 4 inclinations, n^2 over +-12 M with
     refinement; halo parameters jittered x U(0.8, 1.2) in image order

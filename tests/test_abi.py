@@ -106,6 +106,13 @@ def test_argument_errors_return_before_device_work(B):
     assert shadow(bad, cam, it, 1.0, 9.0, 1e-6) == 2
     assert shadow(st, far, it, 1.0, 9.0, 1e-6) == 3
     assert shadow(st, cam, it, 1.0, 9.0, 1e-6) == 4
+    # geometry scan (Sec. 2.3): sizes and missing arrays are rejected on the host
+    assert lib.bh_geometry_scan(-1, None, 0, None, None, None, None, None, None, None,
+                                None) == 1
+    assert lib.bh_geometry_scan(4, None, 0, None, None, None, None, None, None, None,
+                                None) == 1
+    assert lib.bh_geometry_scan(0, None, -1, None, None, None, None, None, None, None,
+                                None) == 1
 
 
 def test_workspace_sizes(B):
