@@ -217,7 +217,8 @@ bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh
  * (DEVICE array of structs, any mix of families), one thread each.  Per
  * spacetime: R_e[i], the extremal radius (the maximiser of -R^2 H(R) on
  * (0, 50], where Eq. 36 holds), chi_e[i] = sqrt(-R_e^2 H(R_e)) (Eq. 37, 0 if
- * -R^2 H never becomes positive), r_plus[i] = R_+, the largest root of
+ * -R^2 H never becomes positive; R_e then only marks where the scan's
+ * maximum fell and has no meaning), r_plus[i] = R_+, the largest root of
  * Delta = R^2 H + chi^2 below R = 50 (Eq. 33; 0 if none), and for each of the
  * n_theta polar angles theta[k] (device, radians) the outer stationary-limit
  * radius R_s[i*n_theta + k], the largest root of R^2 H + chi^2 cos^2 theta

@@ -64,11 +64,12 @@ def test_volumetric_fp64_image(B, oracle, metric, incl):
     assert np.all(gpu["I_n"] == 0.0)
     assert np.array_equal(gpu["refine_level"], ref["level"])
     # the geodesic is the thin-disk mode's: same classes and transfer radii
+    # (to the transfer-map bar: the step sequences differ)
     thin = _gpu_image(B, dict(flat, volumetric=0))
     assert np.array_equal(thin["status"], gpu["status"])
     assert np.array_equal(thin["ncross"], gpu["ncross"])
     has = gpu["ncross"] > 0
-    assert np.allclose(thin["R_em"][0][has], gpu["R_em"][0][has], rtol=1e-7)
+    assert np.allclose(thin["R_em"][0][has], gpu["R_em"][0][has], rtol=TOL_FP64)
 
 
 @pytest.mark.parametrize("metric,incl", [(0, 80.0), (2, 17.0)])
@@ -119,8 +120,13 @@ def test_volumetric_points_thin_layer(B, oracle, precision):
         for n in range(min(int(r["ncross"]), 3)):
             pred[k] += r["I_n"][n] * math.sqrt(2 * math.pi) * 1e-3 / (
                 r["R_em"][n] * abs(r["thdot"][n]))
+    # the limit is exact only as H -> 0: where a ray grazes the layer or
+    # crosses it at a taper the oracle itself departs from it, so each point
+    # may depart by twice the oracle's own departure plus the bar
     lim_tol = 2e-4 if precision else 1e-5
-    assert np.allclose(g_vol["I_tot"][keep], pred[keep], rtol=lim_tol, atol=0.0)
+    own = np.abs(r_vol["I_tot"] - pred)
+    assert np.all(np.abs(g_vol["I_tot"] - pred)[keep] <= (lim_tol * np.abs(pred) + 2 * own)[keep])
+    assert np.count_nonzero(own[keep] <= 1e-5 * np.abs(pred[keep])) >= 0.9 * keep.sum()
 
 
 def test_volumetric_argument_checks(B):
