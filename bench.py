@@ -747,6 +747,112 @@ def run_scan(args, B, workloads, dev, stream):
     print(json.dumps(line), flush=True)
 
 
+METRIC_VISCURVES = ("amplitude-curve points/s (Fig. 12: V(q) and the u cut, 256 q x 256 angles, "
+                    "split BF16 tensor cores)")
+WORKLOAD_VISCURVES = ("Fig. 12 images: {Kerr, Einasto lam_E=0.1, cored-NFW eta=0.02 lam_c=10} "
+                      "at a=0.95, incl 70 deg, 1024^2 over +-12 M, 3 refinement levels (mixed "
+                      "path); 256 radii q in (0, 0.5] cycles/M, 256 position angles each")
+
+
+def run_viscurves(args, B, workloads, dev, stream):
+    """Sec. 6.4's azimuthally averaged amplitude and horizontal cut of the three
+    Fig. 12 images, 256 radii x 256 angles each, on the split BF16 tensor-core
+    path; the FP64 direct mode on the same call is the accuracy reference."""
+    import numpy as np
+    import torch
+
+    from oracle.visibility import amplitude_curves
+    flats = workloads.fig12_images()
+    items = [B.from_flat(d) for d in flats]
+    with torch.cuda.stream(stream):
+        imgs = [o["I"] for o in B.trace_batch(items, device=dev, stream=stream)]
+    n_q, n_phi = 256, 256
+    q = np.linspace(0.5 / n_q, 0.5, n_q)
+    K = n_q * (n_phi + 1) + 1
+    imax = [float(I.abs().max()) for I in imgs]
+    out = [None] * len(imgs)
+
+    def step():
+        for i, I in enumerate(imgs):
+            out[i] = B.visibility_curves(I, items[i][1], q, n_phi=n_phi, mode=B.VIS_BF16,
+                                         image_max=imax[i], stream=stream, check=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        ms = _events_ms(stream, step, args.steps)
+        clocks = sampler.stop()
+        bf = [(a.cpu().numpy(), c.cpu().numpy()) for a, c in out]
+        t0 = time.perf_counter()
+        ref = [B.visibility_curves(I, items[i][1], q, n_phi=n_phi, mode=B.VIS_FP64,
+                                   image_max=imax[i], stream=stream) for i, I in enumerate(imgs)]
+        torch.cuda.synchronize(dev)
+        fp64_s = time.perf_counter() - t0
+        ref = [(a.cpu().numpy(), c.cpu().numpy()) for a, c in ref]
+        # end to end: the images from pinned host memory, the curves back
+        host = [I.cpu().pin_memory() for I in imgs]
+        torch.cuda.synchronize(dev)
+        n_e2e = max(1, min(3, args.steps))
+        w0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for i, h in enumerate(host):
+                a, c = B.visibility_curves(h.to(dev, non_blocking=True), items[i][1], q,
+                                           n_phi=n_phi, mode=B.VIS_BF16, image_max=imax[i],
+                                           stream=stream, check=False)
+                a.cpu(), c.cpu()
+            torch.cuda.synchronize(dev)
+        w1 = time.perf_counter()
+    err = max(float(np.max(np.abs(b[0] - r[0]))) for b, r in zip(bf, ref))
+    err_cut = max(float(np.max(np.abs(b[1] - r[1]))) for b, r in zip(bf, ref))
+    n = flats[0]["nx"]
+    tc_flop = len(imgs) * 3 * 4.0 * n * n * K     # three split products per image
+    achieved = tc_flop / (ms / 1e3) / 1e12
+    peak = _measured_peak("bf16_tflops") or 1900.0
+    # the oracle's direct sums on a bounded sample: a few radii of one image
+    I0 = imgs[0].double().cpu().numpy()
+    g = flats[0]
+    t_end = time.time() + args.cpu_seconds
+    cpu_pts, cpu_t = 0, 0.0
+    rng = np.random.default_rng(3)
+    while time.time() < t_end:
+        qs = q[rng.integers(0, n_q, 1)]
+        t0 = time.perf_counter()
+        amplitude_curves(I0, g["x_min"], g["x_max"], g["y_min"], g["y_max"], qs, 16)
+        cpu_t += time.perf_counter() - t0
+        cpu_pts += 17 / (n_phi + 1)      # 16 angles and the cut of one radius
+    line = {
+        "metric": METRIC_VISCURVES, "value": len(imgs) * n_q / (ms / 1e3),
+        "unit": "curve points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3 split, f32 accumulate", "data": "synthetic",
+        "config": {"workload": WORKLOAD_VISCURVES, "images": len(imgs), "n_q": n_q,
+                   "n_phi": n_phi, "baselines_per_image": K,
+                   "l2": "images 4 MB each, re-read per 256-baseline tile; no flush",
+                   "parallelism": "dp1"},
+        "visibilities_per_s": len(imgs) * K / (ms / 1e3),
+        "max_abs_err_avg_vs_fp64": err, "max_abs_err_cut_vs_fp64": err_cut,
+        "fp64_direct_s_for_same_curves": fp64_s,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "vis_tc_kernel",
+                     "tensor_flop_per_step": tc_flop,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+        "cpu_baseline": {"value": cpu_pts / cpu_t, "unit": "curve points/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"direct FP64 sums (numpy) at random radii of the Kerr image, "
+                                   f"16 angles + cut each, scaled to {n_phi} angles; "
+                                   f"{cpu_t:.1f} s"},
+        "clocks": clocks,
+        "e2e": {"value": n_e2e * len(imgs) * n_q / (w1 - w0), "unit": "curve points/s",
+                "h2d_bytes_per_step": int(len(imgs) * n * n * 4 + len(imgs) * n_q * 8),
+                "d2h_bytes_per_step": int(len(imgs) * 2 * n_q * 8)},
+        "gpu_launches": 3 * len(imgs) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _measured_peak(key):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -794,7 +900,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--workload", choices=["sweep512", "sweep96", "vis1024", "adjoint256", "kerr64",
-                                           "shadow", "scan"],
+                                           "shadow", "scan", "viscurves"],
                     default="sweep512",
                     help="sweep512: the headline line; sweep96 and vis1024: the batched-sweep "
                          "and visibility measurements")
@@ -839,7 +945,8 @@ def main():
             raise SystemExit(f"--workload {args.workload} runs on one GPU")
         fn = {"sweep96": run_sweep96, "vis1024": run_vis1024,
               "adjoint256": run_adjoint, "kerr64": run_kerr64,
-              "shadow": run_shadow, "scan": run_scan}[args.workload]
+              "shadow": run_shadow, "scan": run_scan,
+              "viscurves": run_viscurves}[args.workload]
         return fn(args, B, workloads, dev, stream)
     vol = args.emission == "volumetric"
     flats = workloads.sweep_512(precision=prec, volumetric=vol)

@@ -22,8 +22,9 @@
  *   - the shadow boundary along screen directions (Sec. 4.1, Eqs. 78-79);
  *   - adaptive refinement of the screen near class boundaries
  *     (Introduction and Sec. 4; the rule is a documented reading);
- *   - image diagnostics (Sec. 6.2-6.3, Eqs. 92-107) and visibilities
- *     (Sec. 6.4, Eqs. 108-109).
+ *   - image diagnostics (Sec. 6.2-6.3, Eqs. 92-107), visibilities
+ *     (Sec. 6.4, Eqs. 108-109) and their azimuthally averaged and
+ *     horizontal-cut amplitude curves (Sec. 6.4).
  * Equation numbers are the paper's, counted in order of appearance.
  *
  * Conventions for every entry point:
@@ -392,6 +393,24 @@ bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes);
 bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
                           int32_t mode, double image_max, double* V, void* workspace,
                           size_t workspace_bytes, void* stream);
+
+/* Fourier-domain summaries of Sec. 6.4 at n_q radii q[j] (device doubles,
+ * cycles per M): V_avg[j], the normalised amplitude |V|/|V(0,0)| (Eq. 109)
+ * averaged over the position angle (midpoint rule at phi_k = (k + 1/2) pi /
+ * n_phi, k < n_phi; the amplitude of a real image is symmetric under
+ * (u, v) -> (-u, -v)), and V_cut[j] = |V(q_j, 0)| / |V(0,0)|, the horizontal
+ * cut (device outputs).  The visibilities are those of bh_visibilities in
+ * the given mode (0 FP64 direct, 1 split BF16, 2 split FP16 tensor cores;
+ * image_max > 0 as there), with |V(0,0)| from the same evaluation, so
+ * q = 0 gives 1; an image of zero flux gives NaN.  n_q >= 0, n_phi >= 1.
+ * Needs bh_visibility_curves_workspace_size bytes of 256-byte aligned
+ * workspace; its leading status word is that of bh_visibilities. */
+bh_status bh_visibility_curves_workspace_size(const bh_camera* cam, int32_t n_q, int32_t n_phi,
+                                              size_t* bytes);
+bh_status bh_visibility_curves(const float* I, const bh_camera* cam, int32_t n_q,
+                               const double* q, int32_t n_phi, int32_t mode, double image_max,
+                               double* V_avg, double* V_cut, void* workspace,
+                               size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Gradients by a hand-written discrete adjoint of the FP64 image path.

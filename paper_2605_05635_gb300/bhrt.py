@@ -255,6 +255,11 @@ def lib():
         L.bh_visibilities_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
         L.bh_visibilities.argtypes = [C.c_void_p, P(_Camera), C.c_void_p, C.c_int64, C.c_int32,
                                       C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.bh_visibility_curves_workspace_size.argtypes = [P(_Camera), C.c_int32, C.c_int32,
+                                                          P(C.c_size_t)]
+        L.bh_visibility_curves.argtypes = [C.c_void_p, P(_Camera), C.c_int32, C.c_void_p,
+                                           C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.bh_backward_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
         L.bh_trace_backward.argtypes = [P(_Spacetime), P(_Camera), P(_Emission), P(_Integrator),
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -263,7 +268,8 @@ def lib():
         L.bh_backward_workspace_size.restype = C.c_int
         L.bh_trace_backward.restype = C.c_int
         for fn in ("bh_diagnostics_workspace_size", "bh_diagnostics", "bh_visibilities_fp64",
-                   "bh_visibilities_workspace_size", "bh_visibilities"):
+                   "bh_visibilities_workspace_size", "bh_visibilities",
+                   "bh_visibility_curves_workspace_size", "bh_visibility_curves"):
             getattr(L, fn).restype = C.c_int
         for fn in ("bh_host_geometry", "bh_workspace_size", "bh_trace_image", "bh_trace_batch",
                    "bh_points_workspace_size", "bh_trace_points", "bh_workspace_status",
@@ -614,6 +620,33 @@ def visibilities(I: torch.Tensor, cam: Camera, uv: torch.Tensor, mode: int = VIS
     if check and mode != VIS_FP64:
         _check(lib().bh_workspace_status(C.c_void_p(workspace.data_ptr()), sp), "device status")
     return torch.view_as_complex(out)
+
+
+def visibility_curves(I: torch.Tensor, cam: Camera, q, n_phi: int = 256, mode: int = VIS_BF16,
+                      image_max: Optional[float] = None, stream=None, check: bool = True):
+    """Sec. 6.4's azimuthally averaged normalised amplitude V(q) and horizontal
+    cut |V(q, 0)| / |V(0, 0)| at the radii ``q`` (cycles per M); returns two
+    float64 device tensors."""
+    q_t = torch.as_tensor(q, dtype=torch.float64).reshape(-1).contiguous().to(I.device)
+    n_q = q_t.shape[0]
+    if image_max is None:
+        image_max = float(I.abs().max().item()) or 1.0
+    avg = torch.empty(max(n_q, 1), dtype=torch.float64, device=I.device)
+    cut = torch.empty_like(avg)
+    nb = C.c_size_t(0)
+    _check(lib().bh_visibility_curves_workspace_size(C.byref(cam._c()), n_q, n_phi,
+                                                     C.byref(nb)),
+           "bh_visibility_curves_workspace_size")
+    ws = _aligned_workspace(nb.value, I.device)
+    sp = _stream_ptr(stream)
+    _check(lib().bh_visibility_curves(C.c_void_p(I.data_ptr()), C.byref(cam._c()), n_q,
+                                      C.c_void_p(q_t.data_ptr()), n_phi, mode, image_max,
+                                      C.c_void_p(avg.data_ptr()), C.c_void_p(cut.data_ptr()),
+                                      C.c_void_p(ws.data_ptr()), ws.numel(), sp),
+           "bh_visibility_curves")
+    if check:
+        _check(lib().bh_workspace_status(C.c_void_p(ws.data_ptr()), sp), "device status")
+    return avg[:n_q], cut[:n_q]
 
 
 GRAD_NAMES = ["chi", "incl", "halo1", "halo2", "j0", "p", "R_s", "sigma_in", "sigma_out", "R_out"]

@@ -114,6 +114,15 @@ def vis_1024(precision=1):
                 **EMISSION, **(MIXED_INTEG if precision == 1 else FP64_INTEG))
 
 
+def fig12_images(precision=1, n=1024):
+    """The Fig. 12 images: Kerr, Einasto (lambda_E = 0.1) and cored-NFW at
+    a = 0.95, i = 70 deg, n x n over +-12 M, 4x4 refinement to 3 levels."""
+    return [dict(metric=m, chi=0.95, incl=math.radians(70.0), r_obs=1000.0, nx=n, ny=n,
+                 x_min=-12.0, x_max=12.0, y_min=-12.0, y_max=12.0, levels=3, **HALO[m],
+                 **EMISSION, **(MIXED_INTEG if precision == 1 else FP64_INTEG))
+            for m in (KERR, EINASTO, CNFW)]
+
+
 def uv_points(k, seed, theta_g_muas=3.8, b_max_glambda=15.0):
     """k baselines with |b| ~ U(0, b_max) G-lambda and position angle
     ~ U(0, pi), returned as (u, v) in cycles per M: u = b theta_g."""

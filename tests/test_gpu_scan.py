@@ -66,8 +66,10 @@ def test_mixed_families_against_oracle(B, oracle):
     checked = 0
     for i, P in enumerate(probs):
         ce, Re = oracle.extremal_spin(P)
-        assert res["chi_e"][i] == pytest.approx(ce, rel=1e-12, abs=1e-300)
-        if ce > 0.0:   # else -R^2 H has no positive maximum: R_e is not defined
+        # where -R^2 H never becomes positive chi_e is 0 (the oracle's golden
+        # section returns round-off there) and R_e is not defined
+        assert res["chi_e"][i] == pytest.approx(ce, rel=1e-12, abs=1e-12)
+        if ce > 1e-8:
             assert res["R_e"][i] == pytest.approx(Re, rel=1e-7)
         rp = oracle.horizon(P)
         assert res["flags"][i] == (0 if rp is not None else 1)
