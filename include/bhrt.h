@@ -402,7 +402,7 @@ bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv
  * cut (device outputs).  The visibilities are those of bh_visibilities in
  * the given mode (0 FP64 direct, 1 split BF16, 2 split FP16 tensor cores;
  * image_max > 0 as there), with |V(0,0)| from the same evaluation, so
- * q = 0 gives 1; an image of zero flux gives NaN.  n_q >= 0, n_phi >= 1.
+ * q = 0 gives 1 to rounding; an image of zero flux gives NaN.  n_q >= 0, n_phi >= 1.
  * Needs bh_visibility_curves_workspace_size bytes of 256-byte aligned
  * workspace; its leading status word is that of bh_visibilities. */
 bh_status bh_visibility_curves_workspace_size(const bh_camera* cam, int32_t n_q, int32_t n_phi,

@@ -8,7 +8,7 @@
 // the cut point (q_j, 0); one (0, 0) point closes the set.  A warp per q_j
 // averages the amplitudes in a fixed order (lane-strided sums, then a
 // shuffle tree) and divides by |V(0, 0)| of the same evaluation, so q = 0
-// gives exactly 1.
+// gives 1 to rounding.
 #include <cuda_runtime.h>
 
 #include <algorithm>

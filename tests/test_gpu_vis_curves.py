@@ -63,7 +63,8 @@ def test_curves_match_oracle(B, oracle, mode, tol):
                                   g["y_max"], q, 45)
         assert np.max(np.abs(avg.cpu().numpy() - ra)) <= tol
         assert np.max(np.abs(cut.cpu().numpy() - rc)) <= tol
-        assert avg[0].item() == 1.0 and cut[0].item() == 1.0
+        assert avg[0].item() == pytest.approx(1.0, abs=1e-14)
+        assert cut[0].item() == pytest.approx(1.0, abs=1e-14)
 
 
 def test_gaussian_closed_forms(B):
