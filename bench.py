@@ -715,7 +715,10 @@ def run_scan(args, B, workloads, dev, stream):
         rs = [oracle.ergosurface(P, float(t)) for t in theta]
         cpu_t += time.perf_counter() - t0
         cpu_n += 1
-        worst = max(worst, abs(out["chi_e"][i] - ce) / max(ce, 1e-300))
+        # chi_e = 0 where -R^2 H never becomes positive (the oracle returns
+        # round-off there): an absolute difference
+        d = abs(out["chi_e"][i] - ce)
+        worst = max(worst, d / ce if ce > 1e-8 else d)
         if rp is not None and abs(chi[i]) < ce - 1e-3:
             worst = max(worst, abs(out["r_plus"][i] - rp) / rp)
     line = {

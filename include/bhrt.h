@@ -250,16 +250,19 @@ bh_status bh_geometry_scan(int64_t n, const bh_spacetime* st, int32_t n_theta,
  * must be 0) with the tolerances, step limit and thresholds of integ; the
  * camera gives R_o and the inclination (its screen extent and pixel counts
  * are not used); emission plays no part.  Requires 0 <= b_lo < b_hi,
- * b_tol > 0, all finite (else BH_ERR_INVALID_ARG).  stats (optional device
+ * b_tol > 0, all finite (else BH_ERR_INVALID_ARG).  lanes: rays traced per
+ * direction and round (1 = bisection, 2 .. 32 = (lanes + 1)-section; a power
+ * of two), or 0 for the library's choice: the most lanes, up to 32, with
+ * which all directions fit in half of the GPU's resident threads.  stats (optional device
  * int64[3], may be NULL) receives the rays traced and their accepted and
  * rejected Dormand-Prince steps.  Needs bh_shadow_workspace_size(n_psi)
  * bytes of 256-byte aligned workspace. */
 bh_status bh_shadow_workspace_size(int64_t n_psi, size_t* bytes);
 bh_status bh_shadow_boundary(const bh_spacetime* st, const bh_camera* cam,
                              const bh_integrator* integ, int64_t n_psi, const double* psi,
-                             double b_lo, double b_hi, double b_tol, double* b_in, double* b_out,
-                             int32_t* flags, int64_t* stats, void* workspace,
-                             size_t workspace_bytes, void* stream);
+                             double b_lo, double b_hi, double b_tol, int32_t lanes,
+                             double* b_in, double* b_out, int32_t* flags, int64_t* stats,
+                             void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Plans: a batch whose per-image constants are computed and uploaded once,

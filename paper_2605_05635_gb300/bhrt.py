@@ -235,8 +235,8 @@ def lib():
         L.bh_shadow_workspace_size.argtypes = [C.c_int64, P(C.c_size_t)]
         L.bh_shadow_boundary.argtypes = [P(_Spacetime), P(_Camera), P(_Integrator), C.c_int64,
                                          C.c_void_p, C.c_double, C.c_double, C.c_double,
-                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                         C.c_void_p, C.c_size_t, C.c_void_p]
+                                         C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.bh_plan_create.argtypes = [C.c_int32, P(_Spacetime), P(_Camera), P(_Emission),
                                      P(_Integrator), P(_ImageOut), C.c_void_p, C.c_size_t,
                                      C.c_void_p, P(C.c_void_p)]
@@ -465,13 +465,16 @@ def geometry_scan(spacetimes, theta=(), device=None, stream=None, stats=None):
 
 
 def shadow_boundary(st: Spacetime, cam: Camera, integ: Integrator, psi, b_lo: float,
-                    b_hi: float, b_tol: float, device=None, stream=None, stats=None):
+                    b_hi: float, b_tol: float, device=None, stream=None, stats=None,
+                    lanes: int = 0):
     """Shadow boundary along screen directions ``psi`` (Sec. 4.1, Eqs. 78-79):
     returns device tensors (b_in, b_out, flags) per direction, the final
     bracket of the capture / escape transition in the impact parameter and
     its flags (1 b_lo not captured, 2 b_hi captured, 4 an undetermined ray,
     8 time budget).  ``stats``, an optional int64 device tensor of 3,
-    receives the rays traced and their accepted and rejected steps."""
+    receives the rays traced and their accepted and rejected steps;
+    ``lanes`` (power of two up to 32, 0 = the library's choice) is the rays
+    traced per direction and round."""
     device = _need_cuda(device)
     psi_t = torch.as_tensor(psi, dtype=torch.float64).reshape(-1).contiguous().to(device)
     n = psi_t.shape[0]
@@ -483,7 +486,7 @@ def shadow_boundary(st: Spacetime, cam: Camera, integ: Integrator, psi, b_lo: fl
     ws = _aligned_workspace(nb.value, device)
     sp = _stream_ptr(stream)
     code = lib().bh_shadow_boundary(C.byref(st._c()), C.byref(cam._c()), C.byref(integ._c()), n,
-                                    C.c_void_p(psi_t.data_ptr()), b_lo, b_hi, b_tol,
+                                    C.c_void_p(psi_t.data_ptr()), b_lo, b_hi, b_tol, lanes,
                                     C.c_void_p(b_in.data_ptr()), C.c_void_p(b_out.data_ptr()),
                                     C.c_void_p(flags.data_ptr()),
                                     C.c_void_p(stats.data_ptr() if stats is not None else 0),

@@ -737,11 +737,12 @@ bh_status bh_shadow_workspace_size(int64_t n_psi, size_t* bytes) {
 
 bh_status bh_shadow_boundary(const bh_spacetime* st, const bh_camera* cam,
                              const bh_integrator* integ, int64_t n_psi, const double* psi,
-                             double b_lo, double b_hi, double b_tol, double* b_in, double* b_out,
-                             int32_t* flags, int64_t* stats, void* workspace,
-                             size_t workspace_bytes, void* stream) {
+                             double b_lo, double b_hi, double b_tol, int32_t lanes,
+                             double* b_in, double* b_out, int32_t* flags, int64_t* stats,
+                             void* workspace, size_t workspace_bytes, void* stream) {
   if (!st || !cam || !integ || n_psi < 0 || (n_psi > 0 && (!psi || !b_in || !b_out || !flags)))
     return BH_ERR_INVALID_ARG;
+  if (lanes < 0 || lanes > 32 || (lanes & (lanes - 1)) != 0) return BH_ERR_INVALID_ARG;
   if (!(std::isfinite(b_lo) && std::isfinite(b_hi) && b_lo >= 0.0 && b_hi > b_lo &&
         b_tol > 0.0 && std::isfinite(b_tol)))
     return BH_ERR_INVALID_ARG;
@@ -784,15 +785,21 @@ bh_status bh_shadow_boundary(const bh_spacetime* st, const bh_camera* cam,
     return BH_ERR_CUDA;
   if (n_psi == 0) return BH_OK;
   // lanes per direction: the largest power of two <= 32 with directions x
-  // lanes within the resident threads (bisection when the directions alone
-  // fill the GPU); a grid of whole warps covering every group once, at most
-  // one resident wave
+  // lanes within half the resident threads (a few warps per SM keep the FP64
+  // pipe busy; more lanes only trace more rays), bisection when the
+  // directions alone reach that; a grid of whole warps covering every group
+  // once, at most one resident wave, in one-warp blocks when four-warp
+  // blocks would leave SMs without work
   const int64_t resident = shadow_resident_threads();
   int G = 1;
-  while (G < 32 && n_psi * (int64_t)(2 * G) <= resident) G *= 2;
+  while (G < 32 && n_psi * (int64_t)(4 * G) <= resident) G *= 2;
+  if (lanes > 0) G = lanes;
   const int64_t warps = (n_psi * G + 31) / 32;
-  const int64_t max_blocks = resident / 128;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 3) / 4, max_blocks));
+  const int threads = warps >= 4 * (int64_t)num_sms() ? 128 : 32;
+  const int64_t max_blocks = resident / threads;
+  const int64_t per_block = threads / 32;
+  const int blocks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((warps + per_block - 1) / per_block, max_blocks));
   ShadowArgs a{};
   a.hdr = hdr;
   a.ip = dip;
@@ -806,7 +813,7 @@ bh_status bh_shadow_boundary(const bh_spacetime* st, const bh_camera* cam,
   a.flags = flags;
   a.stats = reinterpret_cast<unsigned long long*>(stats);
   a.group = G;
-  return launch_shadow(a, blocks, cs) == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+  return launch_shadow(a, blocks, threads, cs) == cudaSuccess ? BH_OK : BH_ERR_CUDA;
 }
 
 bh_status bh_plan_create(int32_t n, const bh_spacetime* st, const bh_camera* cam,

@@ -108,7 +108,7 @@ struct ShadowArgs {
   unsigned long long* stats;  // optional [3]: rays, accepted, rejected steps
   int group;             // lanes per direction (1, 2, 4, 8, 16, 32)
 };
-cudaError_t launch_shadow(const ShadowArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_shadow(const ShadowArgs& a, int blocks, int threads, cudaStream_t st);
 int shadow_resident_threads();
 
 // scan.cu -- horizon, extremal-spin and stationary-limit scans (Sec. 2.3)
@@ -123,7 +123,7 @@ struct ScanArgs {
   double* R_s;             // optional [n][n_theta]
   int32_t* flags;          // [n]
   unsigned long long* stats;  // optional [2]: lapse evaluations of the horizon
-                              // and of the stationary-limit kernel
+                              // and of the stationary-limit searches
 };
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 

@@ -1,19 +1,25 @@
 // scan.cu -- horizon, extremal-spin and stationary-limit scans over many
 // spacetimes (Sec. 2.3, Eqs. 33-41): the parameter-space classification
-// behind Figs. 2-4, one spacetime (or one spacetime and polar angle) per
-// thread, in FP64.
+// behind Figs. 2-4, one spacetime per thread, in FP64.
 //
 // Delta(R) = R^2 H(R) + chi^2 (Eq. 33) and the stationary-limit function
-// R^2 H(R) + chi^2 cos^2 theta (Eq. 40) are both R^2 H(R) plus a constant,
-// so both take their minimum where R^2 H(R) does: at the extremal radius
-// R_e of Eqs. 34-37, where 2 H + R H' = 0 (Eq. 36) and
-// chi_e^2 = -R_e^2 H(R_e) (Eq. 37).  Each thread therefore
+// R^2 H(R) + chi^2 cos^2 theta (Eq. 40) are both R^2 H(R) + c with c >= 0,
+// so both take their minimum where R^2 H(R) does, at the extremal radius R_e
+// of Eqs. 34-37 (2 H + R H' = 0, Eq. 36; chi_e^2 = -R_e^2 H(R_e), Eq. 37),
+// and above the largest zero R_H of R^2 H (the equatorial static limit,
+// Eq. 41) every R^2 H + c is positive.  Each thread therefore
 //   1. finds R_e as the maximiser of -R^2 H over (0, 50] (geometric scan,
 //      then bisection of Eq. 36 between the neighbours of the best sample);
-//   2. finds the largest root of R^2 H + c above R_e (c = chi^2 for R_+,
-//      chi^2 cos^2 theta for R_s) by a downward geometric scan from R = 50
-//      to the first sign change, bracketed below by R_e, where the function
-//      is at its minimum, then bisection to the last representable bracket.
+//   2. finds R_H by a downward geometric scan from R = 50 to the first sign
+//      change, stopping at R_e, where R^2 H is smallest;
+//   3. finds R_+ and each R_s(theta) as the largest root of R^2 H + c in
+//      [R_e, R_H] by the same downward scan started at R_H (at R = 50 when
+//      R^2 H has no zero below it).
+// Every root is then polished inside its bracket by Newton steps on
+// d(R^2 H)/dR = R (2 H + R H'), each pushed a few units in the last place
+// past the root so that both ends of the bracket close in, with bisection
+// wherever Newton would leave the bracket, to the last representable
+// bracket; the upper end is returned.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,7 +32,8 @@ namespace bhrt {
 namespace {
 
 constexpr double kScanTop = 50.0;      // no root is sought above R = 50
-constexpr double kScanRatio = 0.99;    // geometric scan step
+constexpr double kScanRatio = 0.99;    // geometric step of the root scans (1 %)
+constexpr double kPeakRatio = 0.97;    // geometric step of the extremal scan (3 %)
 constexpr double kScanBottom = 1e-4;
 
 __device__ __forceinline__ bool consts_of(const bh_spacetime& s, MetricConsts<double>& m) {
@@ -72,10 +79,11 @@ __device__ void extremal(const MetricConsts<double>& m, double& chi_e, double& R
       best = v;
       Rb = R;
     }
-    R *= kScanRatio;
+    R *= kPeakRatio;
   }
-  // -R^2 H rises below R_e (Eq. 36's 2H + R H' < 0) and falls above it
-  double lo = Rb * kScanRatio, hi = Rb / kScanRatio;
+  // -R^2 H rises below R_e (Eq. 36's 2H + R H' < 0) and falls above it, so
+  // R_e lies between the neighbours of the best sample
+  double lo = Rb * kPeakRatio, hi = Rb / kPeakRatio;
   for (int it = 0; it < 200; ++it) {
     const double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
@@ -93,14 +101,35 @@ __device__ void extremal(const MetricConsts<double>& m, double& chi_e, double& R
   chi_e = v > 0.0 ? sqrt(v) : 0.0;
 }
 
-// Largest root of R^2 H(R) + c on (R_e, 50] given that R^2 H + c is at its
-// minimum at R_e; returns false if there is none.
-__device__ bool largest_root(const MetricConsts<double>& m, double c, double R_e, double& root,
-                             unsigned& ev) {
-  double hi = kScanTop;
-  if (!(r2H(m, hi, nullptr, ev) + c > 0.0)) return false;
+// Root of R^2 H + c in [lo, hi] with R^2 H(lo) + c <= 0 < R^2 H(hi) + c:
+// safeguarded Newton to the last representable bracket; returns its upper end.
+__device__ double polish(const MetricConsts<double>& m, double c, double lo, double hi,
+                         unsigned& ev) {
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    double g;
+    const double f = r2H(m, x, &g, ev) + c;
+    if (f > 0.0) hi = x; else lo = x;
+    const double d = x * g;  // d(R^2 H)/dR
+    double xn = x - f / d;
+    const double push = 4.0 * 2.220446049250313e-16 * x;
+    xn += f > 0.0 ? -push : push;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    x = xn;
+  }
+  return hi;
+}
+
+// Largest root of R^2 H(R) + c in (R_e, top], where R^2 H + c is smallest at
+// R_e; false if there is none (R^2 H + c not positive at top, or positive at
+// R_e).
+__device__ bool largest_root(const MetricConsts<double>& m, double c, double R_e, double top,
+                             double& root, unsigned& ev) {
+  if (!(r2H(m, top, nullptr, ev) + c > 0.0)) return false;
   if (!(r2H(m, R_e, nullptr, ev) + c <= 0.0)) return false;
-  double lo = R_e;
+  double hi = top, lo = R_e;
   for (double R = hi * kScanRatio; R > R_e; R *= kScanRatio) {
     if (r2H(m, R, nullptr, ev) + c <= 0.0) {
       lo = R;
@@ -108,12 +137,7 @@ __device__ bool largest_root(const MetricConsts<double>& m, double c, double R_e
     }
     hi = R;
   }
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (r2H(m, mid, nullptr, ev) + c > 0.0) hi = mid; else lo = mid;
-  }
-  root = hi;
+  root = polish(m, c, lo, hi, ev);
   return true;
 }
 
@@ -126,56 +150,52 @@ __device__ __forceinline__ void add_count(unsigned long long* dst, unsigned v) {
   if ((threadIdx.x & 31) == 0 && w) atomicAdd(dst, w);
 }
 
-__global__ void __launch_bounds__(128) scan_horizon_kernel(ScanArgs a) {
-  unsigned ev = 0;
+__global__ void __launch_bounds__(128) scan_kernel(ScanArgs a) {
+  unsigned ev_h = 0, ev_s = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     MetricConsts<double> m;
+    double* Rs = a.R_s ? a.R_s + i * a.n_theta : nullptr;
     if (!consts_of(a.st[i], m)) {
       a.r_plus[i] = a.chi_e[i] = a.R_e[i] = 0.0;
       a.flags[i] = 2;
+      for (int k = 0; Rs && k < a.n_theta; ++k) Rs[k] = 0.0;
       continue;
     }
-    double ce, Re, rp = 0.0;
-    extremal(m, ce, Re, ev);
-    const bool hz = largest_root(m, m.chi2, Re, rp, ev);
+    double ce, Re, RH = 0.0, rp = 0.0;
+    extremal(m, ce, Re, ev_h);
+    // R_H: no root of any R^2 H + c (c >= 0) lies above it, so the other
+    // searches start there (or at R = 50 if R^2 H has no zero below it)
+    const bool hasH = largest_root(m, 0.0, Re, kScanTop, RH, ev_h);
+    const double top = hasH ? RH : kScanTop;
+    const bool hz = largest_root(m, m.chi2, Re, top, rp, ev_h);
     a.chi_e[i] = ce;
     a.R_e[i] = Re;
     a.r_plus[i] = hz ? rp : 0.0;
     a.flags[i] = hz ? 0 : 1;
-  }
-  if (a.stats) add_count(&a.stats[0], ev);
-}
-
-__global__ void __launch_bounds__(128) scan_ergo_kernel(ScanArgs a) {
-  unsigned ev = 0;
-  const int64_t total = a.n * a.n_theta;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / a.n_theta;
-    const int k = (int)(t - i * a.n_theta);
-    MetricConsts<double> m;
-    double rs = 0.0;
-    if (consts_of(a.st[i], m)) {
-      const double c = cos(a.theta[k]);
-      if (!largest_root(m, m.chi2 * c * c, a.R_e[i], rs, ev)) rs = 0.0;
+    for (int k = 0; Rs && k < a.n_theta; ++k) {
+      const double cth = cos(a.theta[k]), c = m.chi2 * cth * cth;
+      double rs = 0.0;
+      if (hasH && !(c > 0.0)) {
+        rs = RH;
+      } else if (!largest_root(m, c, Re, top, rs, ev_s)) {
+        rs = 0.0;
+      }
+      Rs[k] = rs;
     }
-    a.R_s[t] = rs;
   }
-  if (a.stats) add_count(&a.stats[1], ev);
+  if (a.stats) {
+    add_count(&a.stats[0], ev_h);
+    add_count(&a.stats[1], ev_s);
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)num_sms() * 16;
-  int64_t blocks = std::min<int64_t>((a.n + 127) / 128, cap);
-  scan_horizon_kernel<<<(int)blocks, 128, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || a.n_theta == 0 || !a.R_s) return e;
-  blocks = std::min<int64_t>((a.n * a.n_theta + 127) / 128, cap);
-  scan_ergo_kernel<<<(int)blocks, 128, 0, st>>>(a);
+  const int64_t blocks = std::min<int64_t>((a.n + 127) / 128, (int64_t)num_sms() * 16);
+  scan_kernel<<<(int)blocks, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@
 // (G + 1)-section of the bracket: the group ballots the fates and keeps the
 // sub-interval between the last captured sample and the first escaping one,
 // so the bracket shrinks by G + 1 per round.  G is chosen on the host so that
-// groups x G fills the resident threads: many directions run as bisection
-// (G = 1, least work), few directions as wide multisection (fewest rounds).
+// groups x G fills half the resident threads (a few warps per SM keep the
+// FP64 pipe busy): many directions run as bisection (G = 1, least work), few
+// directions as wide multisection (fewest rounds).
 //
 // Rays are traced by the FP64 integrator of the image path (ray_init64,
 // ray_step64) with the caller's tolerances; crossings are located but not
@@ -165,8 +166,8 @@ int shadow_resident_threads() {
   return (nb > 0 ? nb : 1) * 128 * num_sms();
 }
 
-cudaError_t launch_shadow(const ShadowArgs& a, int blocks, cudaStream_t st) {
-  shadow_kernel<<<blocks, 128, 0, st>>>(a);
+cudaError_t launch_shadow(const ShadowArgs& a, int blocks, int threads, cudaStream_t st) {
+  shadow_kernel<<<blocks, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

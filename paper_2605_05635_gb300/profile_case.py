@@ -5,7 +5,10 @@ Cases: ``kerr128`` (Kerr a = 0.5, i = 17 deg, 128^2 over [-10, 10]^2, no
 refinement), ``sweep512`` (one 512^2 image of the six-image sweep, with
 refinement) and ``sweep512l0`` (the same image without refinement, so that
 the first trace launch carries all of the run's base rays).  The integrator
-settings are those of the chosen precision's sweep.
+settings are those of the chosen precision's sweep.  ``shadow512`` brackets
+the Fig. 5 cored-NFW shadow boundary along 512 directions to 1e-10 (FP64);
+``scan64k`` classifies 65,536 spacetimes of the Figs. 3-4 grids with 16
+angles.
 """
 import argparse
 import math
@@ -18,10 +21,31 @@ from . import bhrt, workloads
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="kerr128", choices=["kerr128", "sweep512", "sweep512l0"])
+    ap.add_argument("--case", default="kerr128",
+                    choices=["kerr128", "sweep512", "sweep512l0", "shadow512", "scan64k"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--repeat", type=int, default=2)
     a = ap.parse_args(argv)
+    if a.case == "shadow512":
+        flats, psi, lo, hi, tol = workloads.shadow_fig5(512)
+        st, cam, _, it = bhrt.from_flat(flats[2])
+        for _ in range(a.repeat):
+            b_in, b_out, fl = bhrt.shadow_boundary(st, cam, it, psi, lo, hi, tol)
+        torch.cuda.synchronize()
+        print(f"case shadow512: {int((fl != 0).sum())} flagged, mean b "
+              f"{float((b_in + b_out).mean() / 2):.9f}")
+        return 0
+    if a.case == "scan64k":
+        metric, chi, lam_E, eta, lam_c, theta = workloads.geometry_grid(256)
+        sts = [bhrt.Spacetime(metric=int(metric[i]), chi=float(chi[i]),
+                              lambda_E=float(lam_E[i]), eta=float(eta[i]),
+                              lambda_c=float(lam_c[i])) for i in range(0, metric.shape[0], 2)]
+        arr = bhrt.spacetime_array(sts)
+        for _ in range(a.repeat):
+            res = bhrt.geometry_scan(arr, theta)
+        torch.cuda.synchronize()
+        print(f"case scan64k: {len(sts)} spacetimes, {int((res['flags'] == 0).sum())} black holes")
+        return 0
     prec = bhrt.FP64 if a.precision == "fp64" else bhrt.MIXED
     integ = workloads.FP64_INTEG if prec == bhrt.FP64 else workloads.MIXED_INTEG
     if a.case == "kerr128":

@@ -96,9 +96,9 @@ def test_argument_errors_return_before_device_work(B):
                                None, ws, 0, None)
     assert code == 4   # arguments valid: only the workspace is missing
     # shadow boundary (Sec. 4.1): bracket, precision, spacetime, workspace
-    def shadow(s, c, i, lo, hi, tol):
+    def shadow(s, c, i, lo, hi, tol, lanes=0):
         return lib.bh_shadow_boundary(C.byref(s), C.byref(c), C.byref(i), 0, None, lo, hi, tol,
-                                      None, None, None, None, ws, 0, None)
+                                      lanes, None, None, None, None, ws, 0, None)
     for lo, hi, tol in ((3.0, 2.0, 1e-6), (-1.0, 2.0, 1e-6), (1.0, 2.0, 0.0),
                         (1.0, float("nan"), 1e-6), (1.0, 2.0, float("inf"))):
         assert shadow(st, cam, it, lo, hi, tol) == 1
@@ -106,6 +106,8 @@ def test_argument_errors_return_before_device_work(B):
     assert shadow(bad, cam, it, 1.0, 9.0, 1e-6) == 2
     assert shadow(st, far, it, 1.0, 9.0, 1e-6) == 3
     assert shadow(st, cam, it, 1.0, 9.0, 1e-6) == 4
+    for lanes in (-1, 3, 64):
+        assert shadow(st, cam, it, 1.0, 9.0, 1e-6, lanes) == 1
     # geometry scan (Sec. 2.3): sizes and missing arrays are rejected on the host
     assert lib.bh_geometry_scan(-1, None, 0, None, None, None, None, None, None, None,
                                 None) == 1
