@@ -32,7 +32,7 @@ struct alignas(16) ImgParams {
   double r_plus, R_cap, R_esc, R_in;
   double j0, p, R_s, sig_in, sig_out, R_out;
   double H0, hh;           // disk height H(rho) = H0 + hh rho (Eq. 84)
-  double isig_in, isig_out, iR_s, iR_in;  // reciprocals for the volumetric source
+  double isig_in, isig_out, iR_s, iR_in;  // reciprocals for the emissivity (both modes)
   float vf[10];            // the same emission constants in FP32 (mixed path):
                            // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
   double rtol, atol, thdot_min, dlam_min, promote_R, demote_R;

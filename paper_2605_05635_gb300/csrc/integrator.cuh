@@ -142,39 +142,6 @@ __device__ __forceinline__ MetricConsts<T> metric_consts(const ImgParams& ip) {
   return m;
 }
 
-// Circular equatorial emitter at R (Eqs. 90-91 at theta = pi/2, where
-// d_R g_TT = -H', d_R g_Tphi = chi H', d_R g_phph = 2R - chi^2 H') and the
-// redshift g = (-p.u_obs)/(-p.u_em) with -p.u_obs = E_loc = 1 (Eq. 73).
-// Returns false where no timelike prograde circular orbit exists.
-__device__ __forceinline__ bool emitter_g(const MetricConsts<double>& m, double R, double E,
-                                          double ell, double& g) {
-  double iR = 1.0 / R, H, dH;
-  lapse(m, R, iR, H, dH);
-  double den = 2.0 * R - m.chi2 * dH;
-  double disc = 2.0 * R * dH;
-  if (!(disc >= 0.0) || den == 0.0) return false;
-  double W = (-m.chi * dH + sqrt(disc)) / den;
-  double gtt = -H, gtp = -m.chi * (1.0 - H), gpp = R * R + m.chi2 + m.chi2 * (1.0 - H);
-  double norm = -(gtt + 2.0 * W * gtp + W * W * gpp);
-  if (!(norm > 0.0)) return false;
-  double uT = 1.0 / sqrt(norm);
-  g = 1.0 / (uT * (E - W * ell));
-  return true;
-}
-
-// Thin-disk emissivity, Eqs. (83)-(86) at z = 0, rho = R.
-__device__ __forceinline__ double emissivity_eq(const ImgParams& ip, double R) {
-  double tin = 0.5 * (1.0 + tanh((R - ip.R_in) / ip.sig_in));
-  double tout = 0.5 * (1.0 - tanh((R - ip.R_out) / ip.sig_out));
-  return ip.j0 * pow(R / ip.R_in, -ip.p) * exp(-(R - ip.R_in) / ip.R_s) * tin * tout;
-}
-
-// Source of the volumetric intensity, Eq. (88): g^3 j at (R, theta) with the
-// emissivity of Eqs. (83)-(86) (rho = R |sin theta|, z = R cos theta, so a
-// trial stage past the polar axis is its mirror point) and the circular
-// emitter of Eqs. (90)-(91) at the cylindrical radius rho of the equatorial
-// metric (reading); 0 where no timelike circular orbit exists there.  The
-// tapers are written 0.5 (1 + tanh a) = 1 / (1 + exp(-2 a)).
 // 1 / (1 + e^a) without overflow: with t = e^{-|a|} in (0, 1], it is
 // t / (1 + t) for a >= 0 and 1 / (1 + t) otherwise (the tapers of
 // Eqs. 85-86 as logistic functions, 0.5 (1 + tanh x) = 1 / (1 + e^{-2x})).
@@ -184,6 +151,44 @@ __device__ __forceinline__ double logistic_neg(double a) {
   return a >= 0.0 ? t * s : s;
 }
 
+// Circular equatorial emitter at R (Eqs. 90-91 at theta = pi/2, where
+// d_R g_TT = -H', d_R g_Tphi = chi H', d_R g_phph = 2R - chi^2 H') and the
+// redshift g = (-p.u_obs)/(-p.u_em) with -p.u_obs = E_loc = 1 (Eq. 73).
+// Returns false where no timelike prograde circular orbit exists.
+// Reciprocals by d_rcp and d_rsqrt (no slow-path division).
+__device__ __forceinline__ bool emitter_g(const MetricConsts<double>& m, double R, double E,
+                                          double ell, double& g) {
+  double iR = d_rcp(R), H, dH;
+  lapse(m, R, iR, H, dH);
+  double den = 2.0 * R - m.chi2 * dH;
+  double disc = 2.0 * R * dH;
+  if (!(disc >= 0.0) || den == 0.0) return false;
+  double W = (-m.chi * dH + sqrt(disc)) * d_rcp(den);
+  double gtt = -H, gtp = -m.chi * (1.0 - H), gpp = R * R + m.chi2 + m.chi2 * (1.0 - H);
+  double norm = -(gtt + 2.0 * W * gtp + W * W * gpp);
+  if (!(norm > 0.0)) return false;
+  double uT = d_rsqrt(norm);
+  g = d_rcp(uT * (E - W * ell));
+  return true;
+}
+
+// Thin-disk emissivity, Eqs. (83)-(86) at z = 0, rho = R: the power and the
+// exponential in log space and the tanh tapers as logistic functions
+// (0.5 (1 + tanh x) = 1 / (1 + e^{-2x})), by the library's own exp and
+// log1p.
+__device__ __forceinline__ double emissivity_eq(const ImgParams& ip, double R) {
+  const double tin = logistic_neg(-2.0 * (R - ip.R_in) * ip.isig_in);    // Eq. (85)
+  const double tout = logistic_neg(2.0 * (R - ip.R_out) * ip.isig_out);  // Eq. (86)
+  const double lnj = -ip.p * d_log1p(R * ip.iR_in - 1.0) - (R - ip.R_in) * ip.iR_s;
+  return ip.j0 * d_exp(lnj) * tin * tout;                                // Eq. (83)
+}
+
+// Source of the volumetric intensity, Eq. (88): g^3 j at (R, theta) with the
+// emissivity of Eqs. (83)-(86) (rho = R |sin theta|, z = R cos theta, so a
+// trial stage past the polar axis is its mirror point) and the circular
+// emitter of Eqs. (90)-(91) at the cylindrical radius rho of the equatorial
+// metric (reading); 0 where no timelike circular orbit exists there.  The
+// tapers are written 0.5 (1 + tanh a) = 1 / (1 + exp(-2 a)).
 static __device__ __noinline__ double vol_source64(const ImgParams& ip, MetricConsts<double> m,
                                                    double E, double ell, double R, double th) {
   double s, c;
@@ -249,33 +254,39 @@ static __device__ __noinline__ void handle_crossing(const ImgParams& ip, const M
   if (!((s0 > 0.0 && s1 <= 0.0) || (s0 < 0.0 && s1 >= 0.0))) return;
   double sig = 1.0;
   if (s1 != 0.0) {
-    double x0 = 0.0, f0 = s0, x1 = 1.0, f1 = s1;
-    for (int it = 0; it < 80; ++it) {
-      double x2 = x1 - f1 * (x1 - x0) / (f1 - f0);
-      if (!(x2 > fmin(x0, x1) && x2 < fmax(x0, x1))) x2 = 0.5 * (x0 + x1);
-      double f2 = dense1(y0[2], y1[2], hf0[2], hf1[2], hd[2], x2) - kHalfPi;
-      if (f2 == 0.0) {
-        x1 = x2;
-        break;
-      }
-      if ((f2 > 0.0) != (f1 > 0.0)) {
-        x0 = x1;
-        f0 = f1;
+    // theta - pi/2 on the continuous extension (dense1) written out as the
+    // quartic s0 + c1 x + c2 x^2 + c3 x^3 + c4 x^4; Newton steps with its
+    // derivative from the secant point, kept inside the sign-change bracket
+    // by bisection, to |dx| <= 1e-15
+    const double r2 = y1[2] - y0[2], A = hf0[2] - r2, Bq = r2 - hf1[2] - A, Cq = hd[2];
+    const double c1 = hf0[2], c2 = Bq + Cq - A, c3 = -(Bq + 2.0 * Cq), c4 = Cq;
+    double lo = 0.0, hi = 1.0, flo = s0;
+    double x = s0 * d_rcp(s0 - s1);
+    for (int it = 0; it < 60; ++it) {
+      const double f = fma(x, fma(x, fma(x, fma(x, c4, c3), c2), c1), s0);
+      if (f == 0.0) break;
+      if ((f > 0.0) == (flo > 0.0)) {
+        lo = x;
+        flo = f;
       } else {
-        f0 *= 0.5;
+        hi = x;
       }
-      x1 = x2;
-      f1 = f2;
-      if (fabs(x1 - x0) <= 1e-15 || fabs(f2) <= 1e-15) break;
+      const double d = fma(x, fma(x, fma(x, 4.0 * c4, 3.0 * c3), 2.0 * c2), c1);
+      double xn = x - f * d_rcp(d);
+      if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+      const bool done = fabs(xn - x) <= 1e-15;
+      x = xn;
+      if (done) break;
     }
-    sig = x1;
+    sig = x;
   }
   double yc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) yc[i] = dense1(y0[i], y1[i], hf0[i], hf1[i], hd[i], sig);
-  double cth = cos(yc[2]);
+  double sth, cth;
+  d_sincos(yc[2], &sth, &cth);
   double Sig = yc[1] * yc[1] + m.chi2 * cth * cth;
-  double thdot = yc[5] / Sig;                                   // Eq. (60)
+  double thdot = yc[5] * d_rcp(Sig);                            // Eq. (60)
   double lamc = lam + sig * h;
   // events count only inside the integration domain R_cap <= R <= R_esc
   bool trusted = yc[1] >= ip.R_cap && yc[1] <= ip.R_esc && fabs(thdot) >= ip.thdot_min &&
@@ -289,8 +300,12 @@ static __device__ __noinline__ void handle_crossing(const ImgParams& ip, const M
   cs.I[0] += In;
   if (n < 3) {
     cs.I[1 + n] = In;
-    double ph = fmod(yc[3], kTwoPi);
+    // phi reduced to [0, 2 pi) by a two-part 2 pi (no slow-path fmod)
+    const double qn = floor(yc[3] * 0.15915494309189533577);
+    double ph = fma(-qn, 6.283185307179586232, yc[3]);
+    ph = fma(-qn, 2.4492935982947064e-16, ph);
     if (ph < 0.0) ph += kTwoPi;
+    if (ph >= kTwoPi) ph -= kTwoPi;
     if (co.pix >= 0) {
       int64_t o = n * co.stride + co.pix;
       if (co.R_em) co.R_em[o] = (float)yc[1];

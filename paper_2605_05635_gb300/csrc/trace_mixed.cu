@@ -67,14 +67,14 @@ __device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, float
 __device__ __forceinline__ bool emitter_g_f(const MetricConsts<float>& m, float R, float E,
                                             float ell, float& g) {
   float H, dH;
-  lapse(m, R, 1.f / R, H, dH);
+  lapse(m, R, __fdividef(1.f, R), H, dH);
   const float den = 2.f * R - m.chi2 * dH, disc = 2.f * R * dH;
   if (!(disc >= 0.f) || den == 0.f) return false;
-  const float W = (-m.chi * dH + sqrtf(disc)) / den;
+  const float W = __fdividef(-m.chi * dH + sqrtf(disc), den);
   const float gtt = -H, gtp = -m.chi * (1.f - H), gpp = R * R + m.chi2 + m.chi2 * (1.f - H);
   const float norm = -(gtt + 2.f * W * gtp + W * W * gpp);
   if (!(norm > 0.f)) return false;
-  g = sqrtf(norm) / (E - W * ell);
+  g = __fdividef(sqrtf(norm), E - W * ell);
   return true;
 }
 
@@ -269,7 +269,7 @@ static __device__ __noinline__ void cross_f32(const ImgParams& ip, const MetricC
   if (s1 != 0.f) {
     float x0 = 0.f, f0 = s0, x1 = 1.f, f1 = s1;
     for (int it = 0; it < 60; ++it) {
-      float x2 = x1 - f1 * (x1 - x0) / (f1 - f0);
+      float x2 = x1 - __fdividef(f1 * (x1 - x0), f1 - f0);
       if (!(x2 > fminf(x0, x1) && x2 < fmaxf(x0, x1))) x2 = 0.5f * (x0 + x1);
       const float f2 = dense(2, x2, kHPh, kHPl);
       if (f2 == 0.f) {
@@ -290,7 +290,7 @@ static __device__ __noinline__ void cross_f32(const ImgParams& ip, const MetricC
   }
   const float Rc = dense(1, sig, 0.f, 0.f);
   const float pth = dense(5, sig, 0.f, 0.f);
-  const float thdot = pth / (Rc * Rc);  // Eq. (60) on the plane (cos theta = 0)
+  const float thdot = __fdividef(pth, Rc * Rc);  // Eq. (60) on the plane (cos theta = 0)
   const double lamc = lam + (double)(sig * h);
   if (!(Rc >= (float)ip.R_cap && Rc <= (float)ip.R_esc && fabsf(thdot) >= (float)ip.thdot_min &&
         (!cs.have_trusted || lamc - cs.lam_last >= ip.dlam_min)))
@@ -298,19 +298,24 @@ static __device__ __noinline__ void cross_f32(const ImgParams& ip, const MetricC
   const int n = cs.ncross;
   float g = 0.f, j = 0.f;
   if (emitter_g_f(m, Rc, Ef, ellf, g)) {
-    const float Rin = (float)ip.R_in;
-    const float tin = 0.5f * (1.f + tanhf((Rc - Rin) / (float)ip.sig_in));
-    const float tout = 0.5f * (1.f - tanhf((Rc - (float)ip.R_out) / (float)ip.sig_out));
-    j = (float)ip.j0 * exp2f(-(float)ip.p * log2f(Rc / Rin)) * __expf(-(Rc - Rin) / (float)ip.R_s) *
-        tin * tout;
+    // Eqs. (83)-(86) at z = 0 in log space, tapers as logistic functions
+    const float* v = ip.vf;  // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
+    const float tin = logistic_neg_f(-2.f * (Rc - v[2]) * v[3]);
+    const float tout = logistic_neg_f(2.f * (Rc - v[5]) * v[4]);
+    j = v[8] * __expf(-v[6] * __logf(Rc * v[9]) - (Rc - v[2]) * v[7]) * tin * tout;
   }
   // the volumetric mode adds no event intensity (its integral is a state)
   const float In = ip.volumetric ? 0.f : g * g * g * j;
   cs.I[0] += (double)In;
   if (n < 3) {
     cs.I[1 + n] = (double)In;
-    float ph = fmodf(dense(3, sig, 0.f, 0.f), 6.28318530717958647692f);
+    // phi reduced to [0, 2 pi) by a two-part 2 pi (no slow-path fmodf)
+    const float phi = dense(3, sig, 0.f, 0.f);
+    const float qn = floorf(phi * 0.159154943f);
+    float ph = fmaf(-qn, 6.28318548f, phi);
+    ph = fmaf(-qn, -1.74845553e-7f, ph);
     if (ph < 0.f) ph += 6.28318530717958647692f;
+    if (ph >= 6.28318530717958647692f) ph -= 6.28318530717958647692f;
     if (co.pix >= 0) {
       const int64_t o = n * co.stride + co.pix;
       if (co.R_em) co.R_em[o] = Rc;
