@@ -49,3 +49,27 @@ def test_aggregate_single_rank():
     torch = pytest.importorskip("torch")
     import bench
     assert bench.aggregate_ranks(123.0, 4.5, 1, torch.device("cpu")) == (123.0, 4.5)
+
+
+def test_added_workload_generators():
+    """The seeded inputs of the shadow, scan and amplitude-curve benches have
+    the shapes and parameters their metric strings state."""
+    import math
+
+    import numpy as np
+
+    from paper_2605_05635_gb300 import workloads
+    flats, psi, lo, hi, tol = workloads.shadow_fig5()
+    assert [d["metric"] for d in flats] == [0, 1, 2] and len(psi) == 4096
+    assert flats[1]["lam_E"] == 0.3 and flats[2]["eta"] == 0.02 and flats[2]["lam_c"] == 10.0
+    assert all(d["chi"] == 0.5 and abs(d["incl"] - math.radians(60.0)) < 1e-15 for d in flats)
+    assert (lo, hi, tol) == (1.0, 9.0, 1e-10) and psi[0] == 0.0 and psi[-1] < 2 * math.pi
+    metric, chi, lam_E, eta, lam_c, theta = workloads.geometry_grid(8, 4)
+    assert metric.shape == (128,) and np.all(metric[:64] == 1) and np.all(metric[64:] == 2)
+    assert chi.min() == 0.0 and chi.max() == 1.2 and lam_E[:64].min() == 0.05
+    assert eta[64:].max() == 0.3 and np.all(lam_c == 10.0) and theta[-1] == 0.5 * math.pi
+    imgs = workloads.fig12_images()
+    assert [d["metric"] for d in imgs] == [0, 1, 2]
+    assert all(d["nx"] == 1024 and d["chi"] == 0.95 and d["levels"] == 3 for d in imgs)
+    vol = workloads.sweep_512(precision=1, volumetric=True)
+    assert all(d["volumetric"] == 1 for d in vol) and len(vol) == 6

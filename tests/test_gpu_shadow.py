@@ -120,3 +120,33 @@ def test_edges(B):
     st, cam, _, it = B.from_flat(dict(flat, precision=1))
     with pytest.raises(B.BHRTError):
         B.shadow_boundary(st, cam, it, psi, 1.0, 9.0, 1e-6)
+
+
+def test_lane_widths_agree(B):
+    """Bisection (1 lane), 4-lane and 32-lane multisection bracket the same
+    transition: each bracket holds the others' midpoints to within b_tol
+    plus the integration slack."""
+    flat = _flat(0, 0.9, 60.0)
+    psi = np.linspace(0.1, 6.2, 19)
+    st, cam, _, it = B.from_flat(flat)
+    tol = 1e-9
+    mids = []
+    for lanes in (1, 4, 32):
+        b_in, b_out, fl = B.shadow_boundary(st, cam, it, psi, 1.0, 9.0, tol, lanes=lanes)
+        assert np.all(fl.cpu().numpy() == 0)
+        w = (b_out - b_in).cpu().numpy()
+        assert np.all((w > 0) & (w <= tol))
+        mids.append(0.5 * (b_in + b_out).cpu().numpy())
+    for m in mids[1:]:
+        assert np.max(np.abs(m - mids[0])) <= tol + 3e-9
+
+
+def test_time_budget_reports_timeout(B):
+    """A device time budget far below the work ends the call early with the
+    workspace status BH_ERR_TIMEOUT (no fault, no hang)."""
+    flat = dict(_flat(2, 0.9, 17.0), time_budget_s=1e-5)
+    st, cam, _, it = B.from_flat(flat)
+    psi = np.linspace(0.0, 2.0 * math.pi, 2048, endpoint=False)
+    with pytest.raises(B.BHRTError) as e:
+        B.shadow_boundary(st, cam, it, psi, 1.0, 9.0, 1e-12)
+    assert e.value.code == 6
