@@ -131,8 +131,8 @@ typedef struct {
   double promote_dr;    /* mixed: FP64 steps while R < R_+ + promote_dr     */
   double time_budget_s; /* device time budget per call (s); 0 = none      */
   int32_t promote_order;/* mixed: rays reaching image order n >= this
-                           (n = N_cross - 1, Sec. 4.2) inside R = 10 take
-                           FP64 steps until outgoing beyond R = 10;
+                           (n = N_cross - 1, Sec. 4.2) inside R = 5 take
+                           FP64 steps until outgoing beyond R = 5;
                            0..1000, 1000 = never                          */
   int32_t reserved;     /* must be 0                                        */
 } bh_integrator;

@@ -21,8 +21,11 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxPrecision = 1;
 // Mixed path: a promoted ray returns to FP32 once it is outgoing beyond this
-// radius (reading: well outside the photon region of every metric here).
-constexpr double kDemoteR = 10.0;
+// radius, and winding rays are promoted only inside it (reading: outside the
+// photon region, whose outermost circular orbit, the retrograde equatorial
+// one, lies within 4 M for Kerr spins up to 1 and moves by a few percent
+// with the halos of the imaging configurations).
+constexpr double kDemoteR = 5.0;
 
 // ---------------------------------------------------------------- geometry
 struct HostMetric {
