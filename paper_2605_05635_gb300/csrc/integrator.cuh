@@ -598,7 +598,8 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     if (vol) r.fI = vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]);
   }
   // null-constraint monitor at the new point (stage 7 = new point, FSAL)
-  float hdv = (float)(fabs(W) / P2oD);
+  // (a monitor to a few digits: FP32 from truncated operands, off the FP64 pipe)
+  float hdv = __fdividef(f32_trunc(fabs(W)), f32_trunc(P2oD));
   if (hdv > r.hdrift) r.hdrift = hdv;
   if (r.y[1] < ip.R_cap) return 2;
   if (r.y[1] > ip.R_esc) return 1;

@@ -479,7 +479,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
         r.fI = vol_source32(ip, mf, r.Ef, r.ellf, r.yh[1], dtheta_eq(r.yh[2], r.yl[2], 0.f));
     }
   }
-  float hdv = fabsf(W) / P2oD;
+  float hdv = __fdividef(fabsf(W), P2oD);
   if (hdv > r.hdrift) r.hdrift = hdv;
   const float R = r.yh[1];
   if (R < c.R_cap) return 2;
