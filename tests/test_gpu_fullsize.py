@@ -64,3 +64,59 @@ def test_fullsize_sweep_sampled_pixels(B, oracle, precision, tol):
                 (img, i, j, float(g["I"][j, i]), ref["val"][k, 0])
             compared += 1
     assert compared >= 30 and skipped_depth <= 6
+
+
+def test_fullsize_shadow_fig5(B, oracle):
+    """The shadow workload as bench.py times it (three spacetimes x 4096
+    directions to 1e-10, the library's lane choice): no flags, brackets at
+    most 1e-10 wide, sampled directions within 1e-10 + 3e-9 of the oracle's
+    bisection."""
+    from paper_2605_05635_gb300 import workloads
+    flats, psi, lo, hi, tol = workloads.shadow_fig5()
+    psi = np.asarray(psi)
+    rng = np.random.default_rng(31)
+    for d in flats:
+        st, cam, _, it = B.from_flat(d)
+        b_in, b_out, fl = (t.cpu().numpy() for t in B.shadow_boundary(st, cam, it, psi, lo, hi,
+                                                                      tol))
+        assert np.all(fl == 0) and np.all((b_out - b_in <= tol) & (b_out > b_in))
+        k = rng.choice(len(psi), 6, replace=False)
+        ref = oracle.shadow_boundary(oracle.problem(**oracle_flat(d, oracle)), psi[k], lo, hi,
+                                     tol)
+        mid = 0.5 * (b_in[k] + b_out[k])
+        assert np.max(np.abs(mid - 0.5 * (ref["b_in"] + ref["b_out"]))) <= tol + 3e-9
+
+
+def test_fullsize_geometry_scan(B, oracle):
+    """The scan workload (2 x 1024^2 spacetimes, 16 angles) in one call:
+    sampled spacetimes against the oracle's horizon, extremal spin and
+    stationary-limit radius."""
+    import math
+
+    import torch
+    from paper_2605_05635_gb300 import workloads
+    metric, chi, lam_E, eta, lam_c, theta = workloads.geometry_grid()
+    n = metric.shape[0]
+    rec = np.zeros(n, dtype=np.dtype([("metric", "<i4"), ("reserved", "<i4"), ("chi", "<f8"),
+                                      ("lambda_E", "<f8"), ("eta", "<f8"), ("lambda_c", "<f8")]))
+    rec["metric"], rec["chi"], rec["lambda_E"], rec["eta"], rec["lambda_c"] = (
+        metric, chi, lam_E, eta, lam_c)
+    st_d = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+    res = {k: v.cpu().numpy() for k, v in B.geometry_scan(st_d, theta).items()}
+    rng = np.random.default_rng(32)
+    checked = 0
+    for i in rng.choice(n, 40, replace=False):
+        P = oracle.problem(metric=int(metric[i]), chi=float(chi[i]), lam_E=float(lam_E[i]),
+                           eta=float(eta[i]), lam_c=float(lam_c[i]))
+        ce, _ = oracle.extremal_spin(P)
+        assert res["chi_e"][i] == pytest.approx(ce, rel=1e-12, abs=1e-12)
+        rp = oracle.horizon(P)
+        assert res["flags"][i] == (0 if rp is not None else 1)
+        if rp is None or abs(chi[i]) > ce - 1e-3:
+            continue
+        checked += 1
+        assert res["r_plus"][i] == pytest.approx(rp, rel=1e-12)
+        k = int(rng.integers(0, len(theta)))
+        assert res["R_s"][i, k] == pytest.approx(oracle.ergosurface(P, float(theta[k])),
+                                                 rel=1e-12)
+    assert checked >= 10
