@@ -120,3 +120,28 @@ def test_fullsize_geometry_scan(B, oracle):
         assert res["R_s"][i, k] == pytest.approx(oracle.ergosurface(P, float(theta[k])),
                                                  rel=1e-12)
     assert checked >= 10
+
+
+def test_fullsize_amplitude_curves(B):
+    """The amplitude-curve workload (Fig. 12 images at 1024^2, 256 radii x 256
+    angles) on the split BF16 path against the FP64 direct mode of the same
+    call (itself held to the oracle in test_gpu_vis_curves.py), and a few
+    radii of one image against the oracle's direct sums."""
+    from oracle.visibility import amplitude_curves
+    from paper_2605_05635_gb300 import workloads
+    flats = workloads.fig12_images()
+    items = [B.from_flat(d) for d in flats]
+    imgs = [o["I"] for o in B.trace_batch(items)]
+    q = np.linspace(0.5 / 256, 0.5, 256)
+    for I, (_, cam, _, _) in zip(imgs, items):
+        a1, c1 = B.visibility_curves(I, cam, q, n_phi=256, mode=B.VIS_BF16)
+        a0, c0 = B.visibility_curves(I, cam, q, n_phi=256, mode=B.VIS_FP64)
+        assert float((a1 - a0).abs().max()) <= 4e-4
+        assert float((c1 - c0).abs().max()) <= 4e-4
+    d = flats[0]
+    qs = q[[10, 120]]
+    a, c = B.visibility_curves(imgs[0], items[0][1], qs, n_phi=8, mode=B.VIS_FP64)
+    ra, rc = amplitude_curves(imgs[0].double().cpu().numpy(), d["x_min"], d["x_max"], d["y_min"],
+                              d["y_max"], qs, 8)
+    assert np.allclose(a.cpu().numpy(), ra, atol=1e-10) and np.allclose(c.cpu().numpy(), rc,
+                                                                      atol=1e-10)
