@@ -1,6 +1,7 @@
 """Accuracy of the sine/cosine, log(1 + x), exp and reciprocal that the
 tracing kernels use instead of the library functions (Cody & Waite reduction
-with Taylor polynomials; an atanh series; a Newton-refined hardware
+with fitted (FP64) or Taylor (FP32) polynomials; an atanh series; exp by a
+2^(j/32) table and a short Taylor series; a Newton-refined hardware
 reciprocal).  A probe kernel built from the same header evaluates them on the
 GPU; the reference is numpy (FP64, and FP64 at the float arguments for the
 FP32 versions; exact rationals where FP64 itself is the subject).
