@@ -438,10 +438,17 @@ def geometry_scan(spacetimes, theta=(), device=None, stream=None, stats=None):
     device = _need_cuda(device)
     if isinstance(spacetimes, torch.Tensor):
         st_d = spacetimes
+        if (st_d.dtype != torch.uint8 or not st_d.is_cuda or not st_d.is_contiguous()
+                or st_d.numel() % C.sizeof(_Spacetime)):
+            raise ValueError("spacetimes must be a contiguous CUDA uint8 tensor of whole "
+                             "bh_spacetime structs (see spacetime_array)")
         n = st_d.numel() // C.sizeof(_Spacetime)
     else:
         n = len(spacetimes)
         st_d = spacetime_array(spacetimes, device)
+    if stats is not None and (stats.dtype != torch.int64 or not stats.is_cuda
+                              or stats.numel() < 2):
+        raise ValueError("stats must be an int64 CUDA tensor of at least 2 elements")
     th = torch.as_tensor(theta, dtype=torch.float64).reshape(-1).contiguous().to(device)
     k = th.shape[0]
     out = {name: torch.empty(max(n, 1), dtype=torch.float64, device=device)
@@ -476,6 +483,9 @@ def shadow_boundary(st: Spacetime, cam: Camera, integ: Integrator, psi, b_lo: fl
     ``lanes`` (power of two up to 32, 0 = the library's choice) is the rays
     traced per direction and round."""
     device = _need_cuda(device)
+    if stats is not None and (stats.dtype != torch.int64 or not stats.is_cuda
+                              or stats.numel() < 3):
+        raise ValueError("stats must be an int64 CUDA tensor of at least 3 elements")
     psi_t = torch.as_tensor(psi, dtype=torch.float64).reshape(-1).contiguous().to(device)
     n = psi_t.shape[0]
     b_in = torch.empty(max(n, 1), dtype=torch.float64, device=device)
@@ -630,6 +640,8 @@ def visibility_curves(I: torch.Tensor, cam: Camera, q, n_phi: int = 256, mode: i
     """Sec. 6.4's azimuthally averaged normalised amplitude V(q) and horizontal
     cut |V(q, 0)| / |V(0, 0)| at the radii ``q`` (cycles per M); returns two
     float64 device tensors."""
+    if I.dtype != torch.float32 or not I.is_cuda or not I.is_contiguous():
+        raise ValueError("I must be a contiguous float32 CUDA tensor")
     q_t = torch.as_tensor(q, dtype=torch.float64).reshape(-1).contiguous().to(I.device)
     n_q = q_t.shape[0]
     if image_max is None:
