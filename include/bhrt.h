@@ -253,10 +253,10 @@ bh_status bh_geometry_scan(int64_t n, const bh_spacetime* st, int32_t n_theta,
  * b_tol > 0, all finite (else BH_ERR_INVALID_ARG).  lanes: rays traced per
  * direction and round (1 = bisection, 2 .. 32 = (lanes + 1)-section; a power
  * of two), or 0 for the library's choice: the most lanes, up to 32, with
- * which all directions fit in half of the GPU's resident threads.  stats (optional device
- * int64[3], may be NULL) receives the rays traced and their accepted and
- * rejected Dormand-Prince steps.  Needs bh_shadow_workspace_size(n_psi)
- * bytes of 256-byte aligned workspace. */
+ * which all directions fit in half of the GPU's resident threads.  stats
+ * (optional device int64[3], may be NULL) receives the rays traced and their
+ * accepted and rejected Dormand-Prince steps.  Needs
+ * bh_shadow_workspace_size(n_psi) bytes of 256-byte aligned workspace. */
 bh_status bh_shadow_workspace_size(int64_t n_psi, size_t* bytes);
 bh_status bh_shadow_boundary(const bh_spacetime* st, const bh_camera* cam,
                              const bh_integrator* integ, int64_t n_psi, const double* psi,
