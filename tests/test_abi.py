@@ -117,6 +117,30 @@ def test_argument_errors_return_before_device_work(B):
                                 None) == 1
 
 
+def test_added_entry_points_host_checks(B):
+    """Sizes and argument checks of the shadow, scan and amplitude-curve entry
+    points, all answered on the host before any device work."""
+    lib = B.lib()
+    cam = B.Camera(nx=64, ny=48)._c()
+    n = C.c_size_t(0)
+    assert lib.bh_shadow_workspace_size(100, C.byref(n)) == 0 and n.value >= 256
+    assert lib.bh_shadow_workspace_size(-1, C.byref(n)) == 1
+    assert lib.bh_visibility_curves_workspace_size(C.byref(cam), 10, 16, C.byref(n)) == 0
+    # room for the (u, v) set and the visibilities: 10 radii x 17 points + (0, 0)
+    assert n.value >= 2 * (10 * 17 + 1) * 16
+    for nq, nphi in ((-1, 16), (10, 0)):
+        assert lib.bh_visibility_curves_workspace_size(C.byref(cam), nq, nphi, C.byref(n)) == 1
+    fake = C.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    def curves(I, nq, nphi, mode, imax, ws, wsb):
+        return lib.bh_visibility_curves(I, C.byref(cam), nq, fake if nq else None, nphi, mode,
+                                        imax, fake if nq else None, fake if nq else None, ws,
+                                        wsb, None)
+    assert curves(None, 4, 8, 1, 1.0, fake, 1 << 30) == 1            # no image
+    assert curves(fake, 4, 0, 1, 1.0, fake, 1 << 30) == 1            # no angles
+    assert curves(fake, 4, 8, 3, 1.0, fake, 1 << 30) == 1            # unknown mode
+    assert curves(fake, 4, 8, 1, 1.0, None, 0) == 4                  # no workspace
+
+
 def test_workspace_sizes(B):
     cam = B.Camera(nx=64, ny=48, refine_levels=2)
     n64 = B.workspace_bytes([cam], B.Integrator(precision=0))
