@@ -200,23 +200,31 @@ def _subtree_changed(a, b, nx, ny):
     return mask.reshape(ny, nx)
 
 
-def compare_with_fp64(B, workloads, flats, plan, dev, stream, value):
-    """The same images by the all-FP64 path at its own tolerance (rtol 1e-10):
-    its throughput, and the mixed images' intensity error relative to each
-    image's maximum.  Pixels whose class or refinement depth differs are
-    counted, not measured; pixels whose refined subtree differs (a refined
-    cell changed class, which near the critical curve a perturbation of
-    1e-7 already does) are measured separately."""
+def _run_plan_once(B, flats, dev, stream):
+    """One launch of a plan over ``flats``: (plan, stats, seconds)."""
     import torch
-    ref_items = [B.from_flat(dict(d, **workloads.FP64_INTEG)) for d in flats]
-    rp = B.Plan(ref_items, device=dev, keys_cap=KEYS_CAP)
+    plan = B.Plan([B.from_flat(d) for d in flats], device=dev, keys_cap=KEYS_CAP)
     with torch.cuda.stream(stream):
         torch.cuda.synchronize(dev)
         c0 = time.perf_counter()
-        rp.launch(stream=stream)
-        st = rp.stats(stream)
+        plan.launch(stream=stream)
+        st = plan.stats(stream)
         c1 = time.perf_counter()
-    errs, errs_tree, p999, p9999, over, excluded, tree_changed, total = [], [], [], [], 0, 0, 0, 0
+    plan.check(stream)
+    return plan, st, c1 - c0
+
+
+def compare_with_fp64(B, workloads, flats, plan, dev, stream, value, mixed_s_per_step):
+    """The mixed images against the all-FP64 path at its own tolerance (rtol
+    1e-10), pixel by pixel over every pixel of every image: the intensity
+    error relative to each image's maximum with no pixel exempt
+    (``within_bar``: all pixels within 1e-4), the pixels whose base class,
+    refinement depth or refined subtree differ (counted), and the two speed
+    ratios: against FP64 at rtol 1e-10 (precision and tolerance together) and
+    against FP64 at the mixed path's own tolerances (precision alone)."""
+    import torch
+    rp, st, s64 = _run_plan_once(B, [dict(d, **workloads.FP64_INTEG) for d in flats], dev, stream)
+    errs, p999, p9999, over, cls_changed, tree_changed, total = [], [], [], 0, 0, 0, 0
     worst = None
     for img, (a, b) in enumerate(zip(plan.outputs, rp.outputs)):
         same = ((a["status"] == b["status"]) & (a["ncross"] == b["ncross"]) &
@@ -224,34 +232,39 @@ def compare_with_fp64(B, workloads, flats, plan, dev, stream, value):
         tree = same & ~torch.from_numpy(_subtree_changed(a, b, flats[img]["nx"],
                                                          flats[img]["ny"])).to(same.device)
         d = (a["I"].double() - b["I"].double()).abs() / b["I"].double().abs().max()
-        dm = torch.where(same, d, torch.zeros_like(d))
-        k = int(torch.argmax(dm))
-        jj, ii = divmod(k, dm.shape[1])
-        if worst is None or float(dm.flatten()[k]) > worst["err"]:
-            worst = {"err": float(dm.flatten()[k]), "image": img, "i": ii, "j": jj,
+        k = int(torch.argmax(d))
+        jj, ii = divmod(k, d.shape[1])
+        if worst is None or float(d.flatten()[k]) > worst["err"]:
+            worst = {"err": float(d.flatten()[k]), "image": img, "i": ii, "j": jj,
                      "I_mixed": float(a["I"][jj, ii]), "I_fp64": float(b["I"][jj, ii]),
                      "ncross": int(b["ncross"][jj, ii]), "status": int(b["status"][jj, ii]),
                      "level": int(b["refine_level"][jj, ii]),
-                     "subtree_changed": bool(not tree[jj, ii])}
-        errs.append(float(d[same].max()))
-        errs_tree.append(float(d[tree].max()))
-        over += int((dm > 1e-4).sum())
+                     "class_or_depth_changed": bool(not same[jj, ii]),
+                     "subtree_changed": bool(same[jj, ii] and not tree[jj, ii])}
+        errs.append(float(d.max()))
+        over += int((d > 1e-4).sum())
         flat = d.flatten()
         p999.append(float(torch.quantile(flat[::3], 0.999)))
         p9999.append(float(torch.quantile(flat[::3], 0.9999)))
-        excluded += int((~same).sum())
+        cls_changed += int((~same).sum())
         tree_changed += int((same & ~tree).sum())
         total += same.numel()
-    fp64_rate = sum(st["rays"]) / (c1 - c0)
+    fp64_rate = sum(st["rays"]) / s64
     rp.close()
+    # FP64 at the mixed path's own tolerances: the same images with only the
+    # arithmetic precision changed
+    mp, mst, s64m = _run_plan_once(B, [dict(d, precision=0) for d in flats], dev, stream)
+    mp.close()
     return {"fp64_rtol": workloads.FP64_INTEG["rtol"], "fp64_rays_per_s": fp64_rate,
-            "fp64_s_per_step": c1 - c0, "mixed_over_fp64": value / fp64_rate,
+            "fp64_s_per_step": s64, "mixed_over_fp64": value / fp64_rate,
+            "fp64_at_mixed_tolerances_s_per_step": s64m,
+            "mixed_over_fp64_same_tolerances": s64m / mixed_s_per_step,
+            "within_bar": over == 0,
             "max_rel_intensity_err_vs_fp64": max(errs),
-            "max_rel_intensity_err_same_subtree": max(errs_tree),
             "pixels_over_1e-4": over,
             "p99_9_rel_intensity_err_all_pixels": max(p999),
             "p99_99_rel_intensity_err_all_pixels": max(p9999),
-            "pixels_with_class_or_depth_change": excluded,
+            "pixels_with_class_or_depth_change": cls_changed,
             "pixels_with_refined_subtree_change": tree_changed, "pixels": total,
             "worst_pixel": worst}
 
@@ -856,6 +869,68 @@ def run_viscurves(args, B, workloads, dev, stream):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """One fixed case run a few times for profiling a kernel in isolation
+    (``ncu ... python bench.py --profile-case CASE``); prints a one-line
+    summary, no bench line.  Cases: ``kerr128`` (Kerr a = 0.5, i = 17 deg,
+    128^2 over [-10, 10]^2, no refinement), ``sweep512`` (the first image of
+    the 512^2 sweep, with refinement), ``sweep512l0`` (the same image without
+    refinement), ``shadow512`` (the Fig. 5 cored-NFW shadow boundary along
+    512 directions to 1e-10, FP64), ``scan64k`` (65,536 spacetimes of the
+    Figs. 3-4 grids with 16 angles).  Tracing cases use the chosen
+    precision's integrator settings."""
+    import torch
+
+    from paper_2605_05635_gb300 import bhrt, workloads
+    case = args.profile_case
+    if case == "shadow512":
+        flats, psi, lo, hi, tol = workloads.shadow_fig5(512)
+        st, cam, _, it = bhrt.from_flat(flats[2])
+        for _ in range(args.repeat):
+            b_in, b_out, fl = bhrt.shadow_boundary(st, cam, it, psi, lo, hi, tol)
+        torch.cuda.synchronize()
+        print(f"case shadow512: {int((fl != 0).sum())} flagged, mean b "
+              f"{float((b_in + b_out).mean() / 2):.9f}")
+        return 0
+    if case == "scan64k":
+        metric, chi, lam_E, eta, lam_c, theta = workloads.geometry_grid(256)
+        sts = [bhrt.Spacetime(metric=int(metric[i]), chi=float(chi[i]),
+                              lambda_E=float(lam_E[i]), eta=float(eta[i]),
+                              lambda_c=float(lam_c[i])) for i in range(0, metric.shape[0], 2)]
+        arr = bhrt.spacetime_array(sts)
+        for _ in range(args.repeat):
+            res = bhrt.geometry_scan(arr, theta)
+        torch.cuda.synchronize()
+        print(f"case scan64k: {len(sts)} spacetimes, {int((res['flags'] == 0).sum())} black holes")
+        return 0
+    prec = bhrt.FP64 if args.precision == "fp64" else bhrt.MIXED
+    integ = workloads.FP64_INTEG if prec == bhrt.FP64 else workloads.MIXED_INTEG
+    if case == "kerr128":
+        flat = dict(workloads.kerr_64(), nx=128, ny=128, **integ)
+    elif case in ("einasto128", "cnfw128"):
+        # the same screen through the two halo metrics at a = 0.5, i = 17 deg
+        metric = workloads.EINASTO if case == "einasto128" else workloads.CNFW
+        flat = dict(workloads.kerr_64(), nx=128, ny=128, metric=metric, **workloads.HALO[metric],
+                    **integ)
+    else:
+        flat = dict(workloads.sweep_512()[0], **integ)
+        if case == "sweep512l0":
+            flat["levels"] = 0
+    plan = bhrt.Plan([bhrt.from_flat(flat)])
+    for _ in range(args.repeat):
+        plan.launch()
+    torch.cuda.synchronize()
+    plan.check()
+    st = plan.stats()
+    print(f"case {case} {args.precision} (last launch): rays {sum(st['rays'])} accepted fp32 "
+          f"{st['accepted_fp32']} rejected fp32 {st['rejected_fp32']} fp64 "
+          f"{st['accepted_fp64']} rejected fp64 {st['rejected_fp64']} promoted "
+          f"{st['promoted_rays']} lane utilisation fp32 {st['lane_util_fp32']:.3f} "
+          f"fp64 {st['lane_util_fp64']:.3f}")
+    plan.close()
+    return 0
+
+
 def _measured_peak(key):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -912,7 +987,14 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="sweep96: autotune the plan first")
     ap.add_argument("--no-autotune", action="store_true",
                     help="sweep512: keep the default launch shapes")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["kerr128", "einasto128", "cnfw128", "sweep512", "sweep512l0",
+                             "shadow512", "scan64k"],
+                    help="run one fixed case --repeat times for a profiler and exit")
+    ap.add_argument("--repeat", type=int, default=2, help="--profile-case: launches")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.warmup < 3:
         args.warmup = 3
 
@@ -1061,7 +1143,8 @@ def main():
 
     compare = None
     if prec == B.MIXED and not args.no_compare:
-        compare = compare_with_fp64(B, workloads, flats, plan, dev, stream, value)
+        compare = compare_with_fp64(B, workloads, flats, plan, dev, stream, value,
+                                    max_ms / args.steps / 1e3)
 
     if rank == 0:
         cpu = cpu_baseline(flats, args.cpu_seconds) if world == 1 else None

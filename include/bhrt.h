@@ -135,6 +135,21 @@ typedef struct {
                            FP64 steps until outgoing beyond R = 5;
                            0..1000, 1000 = never                          */
   int32_t reserved;     /* must be 0                                        */
+  double promote_turning; /* mixed: radial turning points of near-critical
+                           rays.  With the radial potential of the separated
+                           Hamiltonian (Eqs. 56-59), Rr(R) = P^2 - Delta K =
+                           (Delta p_R)^2, P = (R^2 + chi^2) E - chi ell and K
+                           the Carter-type constant p_th^2 + Q^2, a ray inside
+                           R = 5 takes FP64 steps (until outgoing beyond
+                           R = 5) once Rr < kappa P^2 and Rr'^2 <
+                           2 kappa Rr'' P^2 (Rr'' with Kerr's Delta'' = 2):
+                           it is within kappa of a double root of Rr, i.e.
+                           near the photon orbit, about to turn or to
+                           plunge.  kappa = promote_turning in [0, 1];
+                           0 = off.  Every FP32 -> FP64 hand-off also puts
+                           p_th and p_R back on the ray's FP64 constants
+                           E, ell (Eq. 48) and K from the launch, with
+                           the null condition (Eq. 54).                   */
 } bh_integrator;
 
 /* Per-pixel output planes (device pointers, caller-owned).  Any pointer
@@ -206,7 +221,9 @@ bh_status bh_trace_batch(int32_t n, const bh_spacetime* st, const bh_camera* cam
 
 /* Traces single rays from explicit screen points xy[2*k], xy[2*k+1]
  * (device doubles) into records[k] (device).  Same physics as the image
- * path, no refinement.  Needs bh_points_workspace_size(n) bytes. */
+ * path, no refinement; the mixed precision runs the image path's passes
+ * (FP32, FP64 for promoted rays, FP32 after demotion).  Needs
+ * bh_points_workspace_size(n) bytes (256-byte aligned). */
 bh_status bh_points_workspace_size(int64_t n, size_t* bytes);
 bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh_emission* em,
                           const bh_integrator* integ, int64_t n, const double* xy,
@@ -363,7 +380,10 @@ bh_status bh_diagnostics(const float* I, const bh_camera* cam, double theta_g, d
  * file-scope device array that every GPU loading the library holds until
  * process exit.  The call allocates nothing.  The first call on each device
  * looks the array's device address up (cudaGetSymbolAddress) and caches it,
- * so make that first call before any stream capture.  All calls share the
+ * so make that first call before any stream capture.  The cached address
+ * lives as long as the process: after a cudaDeviceReset of a device (which
+ * reloads the library's device code there) this entry point must not be
+ * used on that device again.  All calls share the
  * array: the histogram is cleared on every call, but calls whose work
  * overlaps on the GPU (different streams, or different host threads on one
  * device) race on it.  Images whose radial profile needs more scratch than
@@ -389,13 +409,17 @@ bh_status bh_visibilities_fp64(const float* I, const bh_camera* cam, const doubl
  *           lose relative precision to the FP16 exponent range).
  * image_max > 0 is the image maximum (or any positive scale near it), used
  * to normalise before splitting.  uv and V as in bh_visibilities_fp64.
+ * Vnorm (optional device double[K], may be NULL) receives the normalised
+ * amplitudes of Eq. (109), |V_k| / |V(0,0)|, with V(0,0) = F = sum I dX dY
+ * (Eq. 92) summed in FP64 from the image (not from the split evaluation);
+ * an image of zero flux gives inf or NaN there.
  * Modes 1-2 need nx <= 4096 and bh_visibilities_workspace_size bytes of
  * 256-byte aligned workspace; a stalled pipeline wait (bounded) sets
  * BH_ERR_TIMEOUT in the workspace status word (bh_workspace_status). */
 bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes);
 bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
-                          int32_t mode, double image_max, double* V, void* workspace,
-                          size_t workspace_bytes, void* stream);
+                          int32_t mode, double image_max, double* V, double* Vnorm,
+                          void* workspace, size_t workspace_bytes, void* stream);
 
 /* Fourier-domain summaries of Sec. 6.4 at n_q radii q[j] (device doubles,
  * cycles per M): V_avg[j], the normalised amplitude |V|/|V(0,0)| (Eq. 109)
@@ -430,8 +454,12 @@ bh_status bh_visibility_curves(const float* I, const bh_camera* cam, int32_t n_q
  * crossings, termination step); R_in = r_ISCO or R_+ + dR_in is
  * differentiated implicitly; the capture radius is held fixed.
  * The forward pass runs in FP64 whatever integ->precision says.  Each ray
- * is replayed with a checkpoint every 64 accepted steps; a ray needing more
- * than 4096 accepted steps or 32 crossings returns BH_ERR_WORKSPACE.
+ * is replayed with a checkpoint every 64 accepted steps into a per-thread
+ * slab sized from the forward image's longest ray (longer rays: fewer
+ * threads share the workspace's checkpoint region); BH_ERR_WORKSPACE only
+ * if one block of 128 such slabs does not fit there (on a 152-SM GPU, a
+ * longest ray of more than about 1.2 million steps, above the default step
+ * limit) or a ray has more than 32 trusted crossings.
  * dL_dI (device float [ny][nx]), dL_ddiag (host, 11) and uv8 (host, 8x2
  * cycles/M) may be NULL; diag11 (host) receives D; image_out (device float
  * [ny][nx]) the forward intensity.  Synchronous: returns when grad10 is

@@ -59,7 +59,8 @@ class _Integrator(C.Structure):
                 ("atol", C.c_double), ("cap_factor", C.c_double), ("esc_factor", C.c_double),
                 ("thetadot_min", C.c_double), ("dlambda_min", C.c_double),
                 ("promote_dr", C.c_double), ("time_budget_s", C.c_double),
-                ("promote_order", C.c_int32), ("reserved", C.c_int32)]
+                ("promote_order", C.c_int32), ("reserved", C.c_int32),
+                ("promote_turning", C.c_double)]
 
 
 class _ImageOut(C.Structure):
@@ -169,12 +170,13 @@ class Integrator:
     promote_dr: float = 0.1
     time_budget_s: float = 0.0
     promote_order: int = 2
+    promote_turning: float = 3e-3
 
     def _c(self):
         return _Integrator(self.precision, self.max_steps, self.rtol, self.atol,
                            self.cap_factor, self.esc_factor, self.thetadot_min,
                            self.dlambda_min, self.promote_dr, self.time_budget_s,
-                           self.promote_order, 0)
+                           self.promote_order, 0, self.promote_turning)
 
 
 def from_flat(d: dict):
@@ -199,7 +201,8 @@ def from_flat(d: dict):
                     dlambda_min=d.get("dlambda_min", 1e-6),
                     promote_dr=d.get("promote_dr", 0.1),
                     time_budget_s=d.get("time_budget_s", 0.0),
-                    promote_order=d.get("promote_order", 2))
+                    promote_order=d.get("promote_order", 2),
+                    promote_turning=d.get("promote_turning", 3e-3))
     return st, cam, em, it
 
 
@@ -254,7 +257,8 @@ def lib():
                                            C.c_void_p, C.c_void_p]
         L.bh_visibilities_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
         L.bh_visibilities.argtypes = [C.c_void_p, P(_Camera), C.c_void_p, C.c_int64, C.c_int32,
-                                      C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                      C.c_void_p]
         L.bh_visibility_curves_workspace_size.argtypes = [P(_Camera), C.c_int32, C.c_int32,
                                                           P(C.c_size_t)]
         L.bh_visibility_curves.argtypes = [C.c_void_p, P(_Camera), C.c_int32, C.c_void_p,
@@ -611,9 +615,10 @@ VIS_FP64, VIS_BF16, VIS_FP16 = 0, 1, 2
 
 def visibilities(I: torch.Tensor, cam: Camera, uv: torch.Tensor, mode: int = VIS_BF16,
                  image_max: Optional[float] = None, stream=None, out=None, workspace=None,
-                 check: bool = True):
+                 check: bool = True, normalised: bool = False):
     """Eq. (108) on the tensor cores (split BF16 / FP16) or by the FP64 direct
-    sum (mode 0); returns a complex128 device tensor."""
+    sum (mode 0); returns a complex128 device tensor, or with ``normalised``
+    the pair (V, |V|/|V(0,0)|) of Eqs. (108)-(109)."""
     uv = uv.to(device=I.device, dtype=torch.float64).contiguous()
     K = uv.shape[0]
     if image_max is None:
@@ -625,14 +630,18 @@ def visibilities(I: torch.Tensor, cam: Camera, uv: torch.Tensor, mode: int = VIS
            "bh_visibilities_workspace_size")
     if workspace is None or workspace.numel() < nb.value:
         workspace = _aligned_workspace(nb.value, I.device)
+    vn = torch.empty(K, dtype=torch.float64, device=I.device) if normalised else None
     sp = _stream_ptr(stream)
     _check(lib().bh_visibilities(C.c_void_p(I.data_ptr()), C.byref(cam._c()),
                                  C.c_void_p(uv.data_ptr()), K, mode, image_max,
-                                 C.c_void_p(out.data_ptr()), C.c_void_p(workspace.data_ptr()),
-                                 workspace.numel(), sp), "bh_visibilities")
+                                 C.c_void_p(out.data_ptr()),
+                                 C.c_void_p(vn.data_ptr() if vn is not None else 0),
+                                 C.c_void_p(workspace.data_ptr()), workspace.numel(), sp),
+           "bh_visibilities")
     if check and mode != VIS_FP64:
         _check(lib().bh_workspace_status(C.c_void_p(workspace.data_ptr()), sp), "device status")
-    return torch.view_as_complex(out)
+    V = torch.view_as_complex(out)
+    return (V, vn) if normalised else V
 
 
 def visibility_curves(I: torch.Tensor, cam: Camera, q, n_phi: int = 256, mode: int = VIS_BF16,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -194,7 +195,8 @@ bh_status validate(const bh_spacetime& s, const bh_camera& c, const bh_emission&
   if (!finite_pos(g.rtol) || !finite_pos(g.atol) || !(g.cap_factor >= 1.0) ||
       !(g.esc_factor > 1.0) || !(g.thetadot_min >= 0.0) || !(g.dlambda_min >= 0.0) ||
       !(g.promote_dr >= 0.0) || !(g.time_budget_s >= 0.0) || g.promote_order < 0 ||
-      g.promote_order > 1000 || g.reserved != 0)
+      g.promote_order > 1000 || g.reserved != 0 ||
+      !(g.promote_turning >= 0.0 && g.promote_turning <= 1.0))
     return BH_ERR_INVALID_ARG;
   return BH_OK;
 }
@@ -272,6 +274,9 @@ bh_status make_params(const bh_spacetime& s, const bh_camera& c, const bh_emissi
   ip.promote_R = rp + g.promote_dr;
   ip.demote_R = kDemoteR;
   ip.promote_ncross = g.promote_order + 1;
+  ip.kappa = g.promote_turning;
+  ip.sin_o = std::sin(c.incl);
+  ip.isin_o = 1.0 / ip.sin_o;
   return BH_OK;
 }
 
@@ -661,9 +666,12 @@ bh_status bh_trace_image(const bh_spacetime* st, const bh_camera* cam, const bh_
   return bh_trace_batch(1, st, cam, em, integ, out, workspace, workspace_bytes, stream);
 }
 
+// Points workspace: header | image constants | two hand-off queues of n
+// records each (the mixed path's FP32 -> FP64 -> FP32 passes).
 bh_status bh_points_workspace_size(int64_t n, size_t* bytes) {
   if (n < 0 || !bytes) return BH_ERR_INVALID_ARG;
-  *bytes = align256(sizeof(WsHeader)) + align256(sizeof(ImgParams));
+  *bytes = align256(sizeof(WsHeader)) + align256(sizeof(ImgParams)) +
+           2 * align256(spill_record_bytes() * (size_t)n);
   return BH_OK;
 }
 
@@ -702,11 +710,32 @@ bh_status bh_trace_points(const bh_spacetime* st, const bh_camera* cam, const bh
   a.rec = records;
   a.head = &hdr->head[0];
   a.source = 0;
-  a.allow_spill = 0;  // points mode: the mixed kernel runs without promotion
+  a.allow_spill = 0;
   a.any_volumetric = em->volumetric;
-  LaunchShape sh{num_sms() * trace_default_blocks_per_sm(integ->precision, 128), 128};
-  cudaError_t e = integ->precision == 0 ? launch_trace_fp64(a, sh, cs) : launch_trace_mixed(a, sh, cs);
-  return e == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+  if (integ->precision == 0) {
+    LaunchShape sh{num_sms() * trace_default_blocks_per_sm(0, 128), 128};
+    return launch_trace_fp64(a, sh, cs) == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+  }
+  // mixed: the image path's three passes (FP32 -> FP64 promoted -> FP32)
+  char* q = ws + align256(sizeof(WsHeader)) + align256(sizeof(ImgParams));
+  SpillRec* q0 = reinterpret_cast<SpillRec*>(q);
+  SpillRec* q1 = reinterpret_cast<SpillRec*>(q + align256(spill_record_bytes() * (size_t)n));
+  LaunchShape s32{num_sms() * trace_default_blocks_per_sm(1, 128), 128};
+  LaunchShape s64{num_sms() * trace_default_blocks_per_sm(0, 128), 128};
+  a.spill_cap = n;
+  for (int pass = 0; pass < 3; ++pass) {
+    TraceArgs b = a;
+    b.head = pass == 0 ? &hdr->head[0] : &hdr->qhead[pass - 1][0];
+    b.source = pass == 0 ? 0 : 1;
+    b.allow_spill = pass < 2 ? 1 : 0;
+    b.spill_in = pass == 1 ? q0 : q1;
+    b.spill_in_count = &hdr->qcount[pass == 1 ? 0 : 1][0];
+    b.spill_out = pass == 0 ? q0 : q1;
+    b.spill_out_count = &hdr->qcount[pass == 0 ? 0 : 1][0];
+    cudaError_t e = pass == 1 ? launch_trace_fp64(b, s64, cs) : launch_trace_mixed(b, s32, cs);
+    if (e != cudaSuccess) return BH_ERR_CUDA;
+  }
+  return BH_OK;
 }
 
 bh_status bh_geometry_scan(int64_t n, const bh_spacetime* st, int32_t n_theta,
@@ -1034,7 +1063,10 @@ namespace {
 
 constexpr int kAdjThreads = 128;
 constexpr int kAdjBlocksPerSM = 2;
-constexpr int kAdjMaxCkpt = 64;  // 64 checkpoints x 64 steps = 4096 accepted steps per ray
+// checkpoint room per adjoint thread in the workspace (64 checkpoints x 64
+// steps = 4096 accepted steps per ray); rays of the forward image that took
+// more steps get larger slabs and the adjoint runs on fewer threads
+constexpr int kAdjMaxCkpt = 64;
 
 // Lapse H(R) for any scalar type: Kerr, Eq. (9) with halo1 = lambda_E,
 // Eq. (13) with halo1 = eta, halo2 = lambda_c.
@@ -1324,12 +1356,25 @@ bh_status bh_trace_backward(const bh_spacetime* st, const bh_camera* cam, const 
   J.base_child = ra.base_child;
   for (int l = 1; l <= kMaxLevels; ++l) J.lv[l] = ra.lv[l];
   J.ckpt = reinterpret_cast<Ckpt*>(ws + BL.ckpt);
-  J.max_ckpt = kAdjMaxCkpt;
   J.grad = reinterpret_cast<double*>(ws + BL.grad);
   J.head = reinterpret_cast<unsigned long long*>(ws + BL.head);
   J.status = reinterpret_cast<int*>(ws + BL.status);
+  // checkpoint slab per thread from the forward image's longest ray (its
+  // attempted steps bound the accepted steps the replay checkpoints): the
+  // workspace's checkpoint region is divided among as many threads as it
+  // can hold such slabs, up to the default grid
+  unsigned long long longest = 0;
+  if (cudaMemcpyAsync(&longest, &ra.hdr->max_ray_steps, sizeof(longest), cudaMemcpyDeviceToHost,
+                      cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return BH_ERR_CUDA;
+  const int64_t room = (int64_t)BL.threads * kAdjMaxCkpt;  // checkpoints in the region
+  const int64_t per = std::max<int64_t>(kAdjMaxCkpt, (int64_t)(longest / kCkptEvery) + 2);
+  int64_t threads = std::min<int64_t>(BL.threads, room / per) / kAdjThreads * kAdjThreads;
+  if (threads < kAdjThreads) return BH_ERR_WORKSPACE;
+  J.max_ckpt = (int)std::min<int64_t>(room / threads, 1 << 30);
   if (cudaMemsetAsync(ws + BL.grad, 0, BL.ckpt - BL.grad, cs) != cudaSuccess) return BH_ERR_CUDA;
-  if (launch_adjoint(J, BL.threads / kAdjThreads, kAdjThreads, cs) != cudaSuccess)
+  if (launch_adjoint(J, (int)(threads / kAdjThreads), kAdjThreads, cs) != cudaSuccess)
     return BH_ERR_CUDA;
   int dstat = 0;
   if (cudaMemcpyAsync(grad10, J.grad, sizeof(double) * 10, cudaMemcpyDeviceToHost, cs) !=

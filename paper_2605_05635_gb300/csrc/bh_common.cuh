@@ -36,6 +36,8 @@ struct alignas(16) ImgParams {
   float vf[10];            // the same emission constants in FP32 (mixed path):
                            // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
   double rtol, atol, thdot_min, dlam_min, promote_R, demote_R;
+  double sin_o, isin_o;    // sin(theta_o) and its reciprocal (launch Carter constant)
+  double kappa;            // mixed: near-double-root threshold of the radial potential
   int32_t promote_ncross;  // mixed: promote once N_cross reaches this inside demote_R
   int32_t volumetric;      // 1: intensity = Eq. (88) integral (seventh ODE component)
 };
@@ -151,15 +153,19 @@ __device__ __forceinline__ void d_sincos(double x, double* s, double* c) {
 // stages around it stay within a few radians): Cody & Waite reduction by
 // the nearest multiple q of pi/2 with a two-part constant, Taylor
 // polynomials of sin r and cos r on |r| <= pi/4 (truncation below 2e-9),
-// then a rotation by q quarter turns.
-__device__ __forceinline__ void d_sincos(float x, float* s, float* c) {
+// then a rotation by q quarter turns.  The argument is an unevaluated sum
+// hi + lo: the leading part of q pi/2 comes off hi exactly (near a multiple
+// of pi/2 the difference is representable), so the reduced argument keeps
+// its relative precision near the poles theta = 0, pi even where hi + lo
+// rounded to one float would carry an absolute error of half an ulp of pi.
+__device__ __forceinline__ void d_sincos2(float hi, float lo, float* s, float* c) {
   // q = nearest integer to 2x/pi, rounded by adding 1.5 * 2^23 (its low
   // mantissa bits then hold q mod 4), so no conversion instruction is needed
-  const float qm = fmaf(x, 0.636619772f, 12582912.0f);     // 2/pi, 1.5 * 2^23
+  const float qm = fmaf(hi + lo, 0.636619772f, 12582912.0f);  // 2/pi, 1.5 * 2^23
   const float q = qm - 12582912.0f;
   const int iq = __float_as_int(qm);
-  float r = fmaf(q, -1.57079637f, x);                      // pi/2, leading part
-  r = fmaf(q, 4.37113883e-8f, r);                          // pi/2, trailing part
+  float r = fmaf(q, -1.57079637f, hi);                     // pi/2, leading part
+  r = fmaf(q, 4.37113883e-8f, r + lo);                     // pi/2, trailing part
   const float r2 = r * r;
   float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
   ps = fmaf(ps, r2, 8.33333333e-3f);                       // 1/5!
@@ -174,6 +180,7 @@ __device__ __forceinline__ void d_sincos(float x, float* s, float* c) {
   *s = (iq & 2) ? -so : so;
   *c = ((iq + 1) & 2) ? -co : co;
 }
+__device__ __forceinline__ void d_sincos(float x, float* s, float* c) { d_sincos2(x, 0.f, s, c); }
 __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 // FP64 reciprocal without a slow path: the hardware's approximate reciprocal
@@ -299,11 +306,10 @@ __device__ __forceinline__ void lapse(const MetricConsts<T>& m, T R, T iR, T& H,
 // theta may leave (0, pi) inside a step (the equations continue through
 // the polar axis; the accepted state is reflected back by the caller).
 // Also returns W = 2 Sigma H and P^2/Delta for the null-constraint monitor.
+// geo_rhs_sc takes sin(theta) and cos(theta) instead of theta.
 template <class T>
-__device__ __forceinline__ bool geo_rhs(const MetricConsts<T>& m, T E, T ell, T R, T th, T pR,
-                                        T pth, T d[6], T& W, T& P2oD) {
-  T s, c;
-  d_sincos(th, &s, &c);
+__device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, T E, T ell, T R, T s, T c,
+                                           T pR, T pth, T d[6], T& W, T& P2oD) {
   T R2 = R * R;
   T Sig = R2 + m.chi2 * c * c;               // Eq. (23)
   // the lapse needs 1/R before Delta exists: 1/R and 1/Sigma from one
@@ -332,6 +338,13 @@ __device__ __forceinline__ bool geo_rhs(const MetricConsts<T>& m, T E, T ell, T 
   d[4] = T(-0.5) * dW_R * iS + W * R * iS2;                       // Eq. (61)
   d[5] = -Q * dQ * iS - W * m.chi2 * s * c * iS2;                 // Eq. (62)
   return (R > T(0)) && (Dl > T(0));
+}
+template <class T>
+__device__ __forceinline__ bool geo_rhs(const MetricConsts<T>& m, T E, T ell, T R, T th, T pR,
+                                        T pth, T d[6], T& W, T& P2oD) {
+  T s, c;
+  d_sincos(th, &s, &c);
+  return geo_rhs_sc(m, E, ell, R, s, c, pR, pth, d, W, P2oD);
 }
 
 // Screen position of a cell from its key (bit-exact cell-centred

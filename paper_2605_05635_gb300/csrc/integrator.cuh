@@ -667,6 +667,69 @@ __device__ __forceinline__ void resume64(const ImgParams& ip, const SpillRec& s,
   r.fI = ip.volumetric ? vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]) : 0.0;
 }
 
+// Carter-type constant K = p_th^2 + Q^2, Q = ell/sin(theta) - chi E sin(theta)
+// (the separation constant of Eq. 56), of the ray launched at the screen point
+// (X, Y): the launch momenta of ray_init64 (Eqs. 70-74) at theta = theta_o, in
+// FP64 and with the same arithmetic, so E and ell here equal the ray's own.
+__device__ __forceinline__ double launch_carter(const ImgParams& ip, double X, double Y) {
+  const double id = d_rsqrt(ip.r_obs * ip.r_obs + X * X + Y * Y);
+  const double pth = ip.sq_gth * (-Y * id);
+  const double ell = ip.sq_gph * (-X * id);
+  const double E = ip.zamo_N + ip.zamo_w * ell;
+  const double Q = ell * ip.isin_o - ip.chi * E * ip.sin_o;
+  return pth * pth + Q * Q;
+}
+
+// Puts a state handed over by the FP32 pass back on its ray's FP64 constants
+// of motion: p_th from K = p_th^2 + Q^2 and p_R from the null condition
+// (Eq. 54 with Eq. 56), Delta^2 p_R^2 = P^2 - Delta K, signs kept; where
+// rounding put the point just beyond a turning point, the momentum there is
+// set to 0 and p_R follows from the K the state then has, so the state stays
+// null.  The FP32 legs integrate with E and ell rounded to floats and round
+// every operation, so their invariants arrive off by about 1e-7; near the
+// photon orbit such an offset would grow exponentially over the windings,
+// whereas an error in the position only shifts the phase along the exact
+// geodesic.
+static __device__ __noinline__ void project_invariants(MetricConsts<double> m, double E,
+                                                       double ell, double K, double* y) {
+  const double R = y[1];
+  double s, c;
+  d_sincos(y[2], &s, &c);
+  if (!(fabs(s) > 1e-8) || !(R > 0.0)) return;
+  double H, dH;
+  lapse(m, R, d_rcp(R), H, dH);
+  const double Dl = R * R * H + m.chi2;                       // Eq. (25)
+  if (!(Dl > 0.0)) return;
+  const double Q = ell * d_rcp(s) - m.chi * E * s;
+  const double pth2 = fmax(K - Q * Q, 0.0);
+  const double Ks = pth2 + Q * Q;
+  const double P = (R * R + m.chi2) * E - m.chi * ell;
+  const double Rr = fmax(P * P - Dl * Ks, 0.0);               // (Delta p_R)^2
+  y[5] = copysign(sqrt(pth2), y[5]);
+  y[4] = copysign(sqrt(Rr) * d_rcp(Dl), y[4]);
+}
+
+// Demotion of a promoted ray that has left a double root of its radial
+// potential: outgoing, with Rr / P^2 = (Delta p_R)^2 / P^2 above
+// kDemoteKappa times the promotion threshold kappa (see the FP32 test
+// near_double_root), i.e. more than about 2 sqrt(kappa / c) away from the
+// photon orbit, where the remaining time near the orbit no longer magnifies
+// a position error.  Evaluated in FP32 from truncated operands (it only
+// decides where the FP32 steps resume).
+constexpr float kDemoteKappa = 16.f;
+static __device__ __noinline__ bool past_double_root(const ImgParams& ip, double E, double ell,
+                                                     double R, double pR) {
+  const MetricConsts<float> m = metric_consts<float>(ip);
+  const float Rf = f32_trunc(R);
+  float H, dH;
+  lapse(m, Rf, __fdividef(1.f, Rf), H, dH);
+  const float R2 = Rf * Rf;
+  const float Dl = R2 * H + m.chi2;
+  const float P = (R2 + m.chi2) * f32_trunc(E) - m.chi * f32_trunc(ell);
+  const float DpR = Dl * f32_trunc(pR);
+  return DpR * DpR > kDemoteKappa * (float)ip.kappa * P * P;
+}
+
 // Resolves a fresh work item to its image, output pixel and screen point.
 __device__ __forceinline__ void resolve_item(const TraceArgs& a, int64_t idx, uint32_t& img,
                                              int64_t& pix, double& X, double& Y) {

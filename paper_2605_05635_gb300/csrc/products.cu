@@ -297,6 +297,14 @@ bh_status bh_diagnostics(const float* I, const bh_camera* cam, double theta_g, d
   size_t need = diag_ws_layout(g, nullptr, nullptr);
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
     return BH_ERR_WORKSPACE;
+  // the profile histogram of pass 2 lives in shared memory: refuse or
+  // configure it before anything is enqueued
+  const size_t smem = (sizeof(double) + sizeof(unsigned)) * g.nbins;
+  if (smem > 200 * 1024) return BH_ERR_INVALID_ARG;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(diag_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return BH_ERR_CUDA;
   DiagWs w;
   diag_ws_layout(g, static_cast<char*>(workspace), &w);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -305,12 +313,6 @@ bh_status bh_diagnostics(const float* I, const bh_camera* cam, double theta_g, d
     return BH_ERR_CUDA;
   diag_pass1<<<kDiagBlocks, kDiagThreads, 0, s>>>(I, g, w);
   diag_mid<<<1, 32, 0, s>>>(g, w);
-  size_t smem = (sizeof(double) + sizeof(unsigned)) * g.nbins;
-  if (smem > 200 * 1024) return BH_ERR_INVALID_ARG;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(diag_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
-    return BH_ERR_CUDA;
   diag_pass2<<<kDiagBlocks, kDiagThreads, smem, s>>>(I, g, w);
   diag_final<<<1, 32, 0, s>>>(g, w, out12);
   return cudaGetLastError() == cudaSuccess ? BH_OK : BH_ERR_CUDA;
@@ -347,7 +349,9 @@ bh_status bh_visibilities_fp64(const float* I, const bh_camera* cam, const doubl
 // kNoAllocScratchBytes long, which every GPU that loads this library keeps
 // until the process exits.  The host needs the array's device address: it is
 // looked up once per device with cudaGetSymbolAddress (the host-side symbol
-// is only a stand-in) and cached.
+// is only a stand-in) and cached for the life of the process; a
+// cudaDeviceReset reloads the module, which makes a cached address stale, so
+// callers that reset a device must not use this entry point on it afterwards.
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 256 * 1024;

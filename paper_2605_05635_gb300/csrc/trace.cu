@@ -55,7 +55,15 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
           img = s.img;
           ip = &a.ip[img];
           m = metric_consts<double>(*ip);
-          resume64(*ip, s, m, r);
+          // a ray promoted from the FP32 pass continues on its exact
+          // constants of motion (K from the launch point)
+          double X, Y;
+          int64_t pix;
+          uint32_t im;
+          resolve_item(a, item, im, pix, X, Y);
+          SpillRec sp = s;
+          project_invariants(m, s.E, s.ell, launch_carter(*ip, X, Y), sp.y);
+          resume64(*ip, sp, m, r);
         } else {
           double X, Y;
           int64_t pix;
@@ -88,8 +96,11 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
         w_rays += 1ull;
         w_max = (unsigned long long)r.steps > w_max ? (unsigned long long)r.steps : w_max;
         active = false;
-      } else if (a.allow_spill && r.nacc != acc0 && r.y[1] > ip->demote_R && r.y[4] > 0.0) {
-        // outgoing beyond the strong-field zone: finish in FP32
+      } else if (a.allow_spill && r.nacc != acc0 && r.y[4] > 0.0 &&
+                 (r.y[1] > ip->demote_R ||
+                  (ip->kappa > 0.0 && past_double_root(*ip, r.E, r.ell, r.y[1], r.y[4])))) {
+        // outgoing beyond the strong-field zone, or away from the double
+        // root of its radial potential: finish in FP32
         unsigned long long slot = atomicAdd(a.spill_out_count, 1ull);
         if (slot < (unsigned long long)a.spill_cap) {
           spill_from64(r, item, img, a.spill_out[slot]);

@@ -50,15 +50,19 @@ struct RhsF {
   float d[6];
   float W, P2;
 };
+// theta is the pair th + thl (see d_sincos2).
 static __device__ __noinline__ RhsF rhs_f32(MetricConsts<float> m, float E, float ell, float R,
-                                            float th, float pR, float pth) {
+                                            float th, float thl, float pR, float pth) {
   RhsF o;
-  geo_rhs(m, E, ell, R, th, pR, pth, o.d, o.W, o.P2);
+  float s, c;
+  d_sincos2(th, thl, &s, &c);
+  geo_rhs_sc(m, E, ell, R, s, c, pR, pth, o.d, o.W, o.P2);
   return o;
 }
 __device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, float E, float ell,
-                                             float R, float th, float pR, float pth, float* d) {
-  const RhsF o = rhs_f32(m, E, ell, R, th, pR, pth);
+                                             float R, float th, float thl, float pR, float pth,
+                                             float* d) {
+  const RhsF o = rhs_f32(m, E, ell, R, th, thl, pR, pth);
 #pragma unroll
   for (int i = 0; i < 6; ++i) d[i] = o.d[i];
 }
@@ -183,7 +187,7 @@ __device__ __forceinline__ void mx_resume(const ImgParams& ip, const SpillRec& s
   x.nacc = s.nacc;
   x.nrej = s.nrej;
   x.steps = s.steps;
-  rhs_f32_into(mf, x.Ef, x.ellf, x.yh[1], x.yh[2], x.yh[4], x.yh[5], x.f);
+  rhs_f32_into(mf, x.Ef, x.ellf, x.yh[1], x.yh[2], x.yl[2], x.yh[4], x.yh[5], x.f);
   if (kVol) {
     df_from(s.I[0], x.Ih, x.Il);
     x.fI = ip.volumetric
@@ -193,9 +197,40 @@ __device__ __forceinline__ void mx_resume(const ImgParams& ip, const SpillRec& s
 }
 
 struct MxConsts {
-  float rtol, atol, R_cap, R_esc, promote_R, demote_R;
+  float rtol, atol, R_cap, R_esc, promote_R, demote_R, kappa;
   int promote_nc;
 };
+
+// Radial turning point of a near-critical ray.  With the radial potential of
+// the separated Hamiltonian (Eq. 56), Rr(R) = (Delta p_R)^2 = P^2 - Delta K
+// (K = p_th^2 + Q^2), a ray whose Rr has a near-double root is close to the
+// photon orbit and about to turn back or to plunge; there its fate and its
+// number of windings depend exponentially on the constants of motion.  In
+// the quadratic model Rr / P^2 = -delta + c (R - R_c)^2, c = Rr'' / (2 P^2),
+// the test Rr < kappa P^2 and Rr'^2 < 2 kappa Rr'' P^2 holds for |delta| <
+// kappa within sqrt(kappa / c) of R_c, and not at the turning points of rays
+// far from critical (there Rr = 0 but Rr'^2 = 4 c delta P^4).  Rr'' takes
+// Kerr's Delta'' = 2 (the halo lapses change it by a few percent): the test
+// only decides where FP64 steps start.  FP32.
+static __device__ __noinline__ bool near_double_root(MetricConsts<float> m, float E, float ell,
+                                                     float R, float th, float pR, float pth,
+                                                     float kappa) {
+  float s, c;
+  d_sincos(th, &s, &c);
+  float H, dH;
+  lapse(m, R, __fdividef(1.f, R), H, dH);
+  const float R2 = R * R;
+  const float Dl = R2 * H + m.chi2, dDl = 2.f * R * H + R2 * dH;  // Eqs. (25), (35)
+  const float P = (R2 + m.chi2) * E - m.chi * ell;
+  const float Q = __fdividef(ell, s) - m.chi * E * s;
+  const float K = pth * pth + Q * Q;
+  const float DpR = Dl * pR;
+  const float Rr = DpR * DpR;
+  const float Rp = 4.f * R * E * P - dDl * K;
+  const float Rpp = 8.f * R2 * E * E + 4.f * E * P - 2.f * K;
+  const float P2 = P * P;
+  return Rr < kappa * P2 && Rpp > 0.f && Rp * Rp < 2.f * kappa * Rpp * P2;
+}
 
 // Launch of the mixed path: the constants of motion and the launch momenta
 // in FP64 (Eqs. 70-74, as in ray_init64), the state as float pairs, and the
@@ -214,7 +249,7 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   df_from(ip.sq_gth * (-Y * id), r.yh[5], r.yl[5]);
   r.Ef = (float)r.E;
   r.ellf = (float)r.ell;
-  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f);
+  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yl[2], r.yh[4], r.yh[5], r.f);
   float d0 = 0.f, d1 = 0.f, sc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -227,7 +262,7 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   d1 = sqrtf(d1 / 6.f);
   const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * __fdividef(d0, d1);
   float f1[6];
-  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1] + h0 * r.f[1], r.yh[2] + h0 * r.f[2],
+  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1] + h0 * r.f[1], r.yh[2], r.yl[2] + h0 * r.f[2],
                r.yh[4] + h0 * r.f[4], r.yh[5] + h0 * r.f[5], f1);
   float d2 = 0.f;
 #pragma unroll
@@ -398,7 +433,10 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     float ys[4];
 #pragma unroll
     for (int x = 0; x < 4; ++x) ys[x] = r.yh[kQC(x)] + (r.yl[kQC(x)] + h * q[0][x]);
-    bool ok = geo_rhs(mf, r.Ef, r.ellf, ys[0], ys[1], ys[2], ys[3], k, W, P2oD);
+    // sin and cos of theta from the pair (state hi, state lo + stage offset)
+    float sth, cth;
+    d_sincos2(r.yh[2], r.yl[2] + h * q[0][1], &sth, &cth);
+    bool ok = geo_rhs_sc(mf, r.Ef, r.ellf, ys[0], sth, cth, ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
     // the source depends on the state only, so its stage-input sum is not needed
     if (vol)
@@ -483,7 +521,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
       df_from(th, r.yh[2], r.yl[2]);
       df_from(pth, r.yh[5], r.yl[5]);
       df_from(ph, r.yh[3], r.yl[3]);
-      rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yh[4], r.yh[5], r.f);
+      rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yl[2], r.yh[4], r.yh[5], r.f);
       if (vol)
         r.fI = vol_source32(ip, mf, r.Ef, r.ellf, r.yh[1], dtheta_eq(r.yh[2], r.yl[2], 0.f));
     }
@@ -499,6 +537,10 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   // image order n = N_cross - 1 (Sec. 4.2): rays winding to n >= promote_order
   // are promoted
   if (may_promote && (R < c.promote_R || (r.cs.ncross >= c.promote_nc && R < c.demote_R)))
+    return 4;
+  // radial turning points of near-critical rays
+  if (may_promote && c.kappa > 0.f && R < c.demote_R &&
+      near_double_root(mf, r.Ef, r.ellf, R, r.yh[2], r.yh[4], r.yh[5], c.kappa))
     return 4;
   return r.steps >= ip.max_steps ? 3 : 0;
 }
@@ -558,6 +600,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
         c.promote_R = (float)ip->promote_R;
         c.demote_R = (float)ip->demote_R;
         c.promote_nc = ip->promote_ncross;
+        c.kappa = (float)ip->kappa;
         active = true;
       } else {
         drained = true;

@@ -431,6 +431,33 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// Normalised amplitudes of Eq. (109), |V_k| / |V(0,0)|, with V(0,0) = F =
+// sum_ij I_ij dX dY (Eq. 92) accumulated in FP64 by one block in a fixed order
+// (so repeated calls agree bit for bit), then one amplitude per thread.
+constexpr int kNormThreads = 1024;
+__global__ void __launch_bounds__(kNormThreads) vis_norm_kernel(const float* __restrict__ I,
+                                                                int64_t npix, double dA,
+                                                                const double* __restrict__ V,
+                                                                int64_t K, double* __restrict__ Vn) {
+  __shared__ double part[kNormThreads / 32];
+  __shared__ double F;
+  double acc = 0.0;
+  for (int64_t p = threadIdx.x; p < npix; p += kNormThreads) acc += (double)I[p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kNormThreads / 32; ++w) t += part[w];
+    F = fabs(t * dA);
+  }
+  __syncthreads();
+  const double f = F;
+  for (int64_t k = threadIdx.x; k < K; k += kNormThreads)
+    Vn[k] = sqrt(V[2 * k] * V[2 * k] + V[2 * k + 1] * V[2 * k + 1]) / f;
+}
+
 extern "C" {
 
 bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes) {
@@ -440,16 +467,12 @@ bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes) {
   return BH_OK;
 }
 
-bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
+namespace {
+
+bh_status vis_contraction(const float* I, const bh_camera* cam, const double* uv, int64_t K,
                           int32_t mode, double image_max, double* V, void* workspace,
                           size_t workspace_bytes, void* stream) {
-  if (!I || !cam || K < 0 || (K > 0 && (!uv || !V)) || cam->nx < 1 || cam->ny < 1 ||
-      (mode != 0 && cam->nx > kVisMaxNx) ||
-      !(cam->x_max > cam->x_min) || !(cam->y_max > cam->y_min) || !(image_max > 0.0) ||
-      !std::isfinite(image_max))
-    return BH_ERR_INVALID_ARG;
   if (mode == 0) return bh_visibilities_fp64(I, cam, uv, K, V, stream);
-  if (mode != 1 && mode != 2) return BH_ERR_INVALID_ARG;
   if (K == 0) return BH_OK;
   size_t need;
   bh_visibilities_workspace_size(cam, &need);
@@ -494,6 +517,25 @@ bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv
   const int64_t grid = (K + kVisUV - 1) / kVisUV;
   if (grid > 0x7fffffff) return BH_ERR_INVALID_ARG;
   vis_tc_kernel<<<(unsigned)grid, kVisThreads, kVisSmem, s>>>(map, a);
+  return cudaGetLastError() == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+}
+
+}  // namespace
+
+bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
+                          int32_t mode, double image_max, double* V, double* Vnorm,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+  if (!I || !cam || K < 0 || (K > 0 && (!uv || !V)) || cam->nx < 1 || cam->ny < 1 ||
+      (mode != 0 && mode != 1 && mode != 2) || (mode != 0 && cam->nx > kVisMaxNx) ||
+      !(cam->x_max > cam->x_min) || !(cam->y_max > cam->y_min) || !(image_max > 0.0) ||
+      !std::isfinite(image_max))
+    return BH_ERR_INVALID_ARG;
+  bh_status st = vis_contraction(I, cam, uv, K, mode, image_max, V, workspace, workspace_bytes,
+                                 stream);
+  if (st != BH_OK || !Vnorm || K == 0) return st;
+  const double dA = ((cam->x_max - cam->x_min) / cam->nx) * ((cam->y_max - cam->y_min) / cam->ny);
+  vis_norm_kernel<<<1, kNormThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      I, (int64_t)cam->nx * cam->ny, dA, V, K, Vnorm);
   return cudaGetLastError() == cudaSuccess ? BH_OK : BH_ERR_CUDA;
 }
 

@@ -27,8 +27,9 @@ FP64_INTEG = dict(precision=0, rtol=1e-10, atol=1e-12, max_steps=1_000_000, cap_
 # Mixed path: FP32 bulk with FP64 promotion; its step tolerances sit above
 # the FP32 round-off floor of the error estimate (an absolute tolerance
 # below about 1e-8 only adds rejected steps where a component passes
-# through zero, without changing the images).
-MIXED_INTEG = dict(FP64_INTEG, precision=1, rtol=1e-8, atol=1e-8)
+# through zero, without changing the images); rays within 3e-3 of a double
+# root of their radial potential take FP64 steps (promote_turning).
+MIXED_INTEG = dict(FP64_INTEG, precision=1, rtol=1e-8, atol=1e-8, promote_turning=3e-3)
 
 
 def kerr_64():

@@ -18,3 +18,18 @@ def oracle():
     import oracle as O
     O.build()
     return O
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Rays waived from exact integer parity, per test and rule (threshold,
+    tolerance_flip, perturbation; see parity.py)."""
+    try:
+        from parity import WAIVERS
+    except ImportError:
+        return
+    terminalreporter.section("integer-parity waivers")
+    if not WAIVERS:
+        terminalreporter.write_line("none")
+        return
+    for test, c in sorted(WAIVERS.items()):
+        terminalreporter.write_line(f"{test}: " + ", ".join(f"{k} {v}" for k, v in sorted(c.items())))

@@ -145,3 +145,118 @@ def test_fullsize_amplitude_curves(B):
                               d["y_max"], qs, 8)
     assert np.allclose(a.cpu().numpy(), ra, atol=1e-10) and np.allclose(c.cpu().numpy(), rc,
                                                                       atol=1e-10)
+
+
+def _key_level(k):
+    return (k >> 12) & 0xF
+
+
+def _key_parent(k):
+    """The cell whose refinement created cell k (level >= 1): level - 1 and
+    that level's digit cleared; a level-1 cell's parent is its base pixel."""
+    L = _key_level(k)
+    sh = 4 * (3 - L)
+    return (k & ~(0xF << sh) & ~(0xF << 12)) | ((L - 1) << 12)
+
+
+def _cell_centre(flat, k):
+    """Screen centre of the cell with key k (cell-centred children)."""
+    nx = flat["nx"]
+    base = k >> 16
+    i, j = base % nx, base // nx
+    X, Y = pixel_centre(flat, i, j)
+    wx = (flat["x_max"] - flat["x_min"]) / nx
+    wy = (flat["y_max"] - flat["y_min"]) / flat["ny"]
+    for lvl in range(1, _key_level(k) + 1):
+        d = (k >> (4 * (3 - lvl))) & 0xF
+        X += ((d & 3) + 0.5) / 4.0 * wx - 0.5 * wx
+        Y += ((d >> 2) + 0.5) / 4.0 * wy - 0.5 * wy
+        wx /= 4.0
+        wy /= 4.0
+    return X, Y
+
+
+def _siblings(k):
+    """The in-block 4-neighbours of a refined cell (same parent)."""
+    L = _key_level(k)
+    sh = 4 * (3 - L)
+    d = (k >> sh) & 0xF
+    cx, cy = d & 3, d >> 2
+    out = []
+    for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+        if 0 <= cx + dx < 4 and 0 <= cy + dy < 4:
+            out.append((k & ~(0xF << sh)) | (((cy + dy) * 4 + cx + dx) << sh))
+    return out
+
+
+def test_fullsize_mixed_every_pixel_vs_fp64(B, oracle):
+    """Every pixel of the six 512^2 images of the benchmark, mixed path (as
+    bench.py times it) against the all-FP64 path at rtol 1e-10 (pinned to the
+    oracle at 1e-6 by the sampled test above and by test_gpu_trace.py):
+
+    - intensity within 1e-4 of each image's maximum on every pixel, none
+      exempt;
+    - base-ray classes equal, except rays the oracle finds class-sensitive
+      at mixed precision (parity.py's counted rule);
+    - refinement keys equal, except where the refinement decision that
+      differs involves a cell the oracle finds class-sensitive (the cell or
+      one of its in-block 4-neighbours, at the cell centre).
+    """
+    import torch
+    from paper_2605_05635_gb300 import workloads
+    cap = 1 << 23
+    outs = {}
+    for prec in (1, 0):
+        flats = workloads.sweep_512(precision=prec)
+        plan = B.Plan([B.from_flat(d) for d in flats], keys_cap=cap)
+        plan.launch()
+        plan.check()
+        outs[prec] = [{k: v.cpu().numpy() for k, v in o.items()} for o in plan.outputs]
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    flats = workloads.sweep_512(precision=1)
+    worst, class_waived, tree_decisions = 0.0, 0, 0
+    for img, d in enumerate(flats):
+        a, b = outs[1][img], outs[0][img]
+        scale = float(np.abs(b["I"]).max())
+        err = np.abs(a["I"].astype(np.float64) - b["I"].astype(np.float64)) / scale
+        worst = max(worst, float(err.max()))
+        assert float(err.max()) <= 1e-4, (img, np.unravel_index(int(err.argmax()), err.shape),
+                                          float(err.max()))
+        bad = np.argwhere((a["status"] != b["status"]) | (a["ncross"] != b["ncross"]))
+        for j, i in bad:
+            assert class_sensitive(oracle, d, *pixel_centre(d, int(i), int(j))), (img, i, j)
+            class_waived += 1
+        ka = a["refine_keys"][: int(a["refine_keys_count"][0])].astype(np.int64)
+        kb = b["refine_keys"][: int(b["refine_keys_count"][0])].astype(np.int64)
+        assert len(ka) <= cap and len(kb) <= cap
+        diff = np.setxor1d(ka, kb)
+        sa, sb = set(ka.tolist()), set(kb.tolist())
+        # refined cells: parents of traced cells
+        ref_a = {_key_parent(k) for k in sa}
+        ref_b = {_key_parent(k) for k in sb}
+        decided = set()
+        for k in diff.tolist():
+            c = _key_parent(k)                 # refined in one run only
+            while _key_level(c) >= 1 and not (c in sa and c in sb):
+                c = _key_parent(c)
+            decided.add(c)
+        for c in decided:
+            assert (c in ref_a) != (c in ref_b)
+            if _key_level(c) == 0:
+                # a base pixel's decision: some base class among it and its
+                # neighbours changed, and each such change was checked above
+                base = c >> 16
+                i, j = base % d["nx"], base // d["nx"]
+                near = [(j, i), (j - 1, i), (j + 1, i), (j, i - 1), (j, i + 1)]
+                assert any(0 <= y < d["ny"] and 0 <= x < d["nx"] and
+                           (a["status"][y, x], a["ncross"][y, x]) !=
+                           (b["status"][y, x], b["ncross"][y, x]) for y, x in near), (img, c)
+                continue
+            cells = [c] + _siblings(c)
+            assert any(class_sensitive(oracle, d, *_cell_centre(d, q)) for q in cells), \
+                (img, hex(c))
+            tree_decisions += 1
+    print(f"mixed vs FP64 on 6 x 512^2: max {worst:.3e} of the image maximum; "
+          f"base classes waived {class_waived}; refinement decisions waived {tree_decisions}")

@@ -140,3 +140,26 @@ def test_visibilities_widest_screen_and_ragged_baselines(B):
     wide = B.Camera(nx=nx + 1, ny=ny, x_min=-12.0, x_max=12.0, y_min=-1.0, y_max=1.0)
     with pytest.raises(B.BHRTError):
         B.visibilities(torch.zeros(ny, nx + 1, device="cuda"), wide, uv, mode=1)
+
+
+@pytest.mark.parametrize("mode,tol", [(0, 1e-12), (1, 2e-4), (2, 2e-4)])
+def test_normalised_amplitudes_match_oracle(B, oracle, mode, tol):
+    """Eq. (109): the normalised amplitude |V|/|V(0,0)| returned beside V,
+    against the oracle's FP64 direct sum divided by its zero-baseline value
+    (the flux, Eq. 92): within 1e-12 for the FP64 mode and within the split
+    modes' bound on |V - V_ref| / |V(0,0)|; 1 at the zero baseline."""
+    import torch
+    from oracle.visibility import visibilities
+    from paper_2605_05635_gb300 import workloads
+    uv = np.concatenate([[[0.0, 0.0]], workloads.uv_points(99, seed=20260514)])
+    for name, I, g in _images(oracle):
+        cam = B.Camera(nx=g["nx"], ny=g["ny"], x_min=g["x_min"], x_max=g["x_max"],
+                       y_min=g["y_min"], y_max=g["y_max"])
+        V, Vn = B.visibilities(torch.from_numpy(I).cuda(), cam, torch.from_numpy(uv), mode=mode,
+                               normalised=True)
+        ref = visibilities(I.astype(np.float64), g["x_min"], g["x_max"], g["y_min"], g["y_max"], uv)
+        want = np.abs(ref) / abs(ref[0])
+        got = Vn.cpu().numpy()
+        assert got.shape == (100,)
+        assert np.max(np.abs(got - want)) <= tol, (name, mode)
+        assert abs(got[0] - 1.0) <= tol

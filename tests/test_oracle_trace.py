@@ -222,3 +222,101 @@ def test_polar_axis_ray_matches_rotated_ray_in_schwarzschild(oracle):
         assert pol["status"] == rot["status"] == (1 if k < 27.0 else 0)
         assert abs(pol["K_final"] - pol["K0"]) <= 1e-9 * pol["K0"]
         assert pol["n_accept"] < 2 * rot["n_accept"]
+
+
+def _schwarzschild_captured(P, X, Y):
+    """Capture class of the Schwarzschild ray through screen point (X, Y) in
+    closed form: the ZAMO launch at (R_o, theta_o) gives E = sqrt(1 - 2/R_o)
+    and K = p_th^2 + ell^2 / sin^2 theta_o = R_o^2 (X^2 + Y^2) / d^2 with
+    d^2 = R_o^2 + X^2 + Y^2 (Eqs. 70-74 at chi = 0); the ray is captured iff
+    K/E^2 < 27 (b < 3 sqrt 3, the photon sphere).  Returns (class, K/E^2)."""
+    Ro = P.r_obs
+    d2 = Ro * Ro + X * X + Y * Y
+    k = Ro * Ro * (X * X + Y * Y) / d2 / (1.0 - 2.0 / Ro)
+    return (k < 27.0).astype(np.int64), k
+
+
+def test_refinement_marking_rule_on_schwarzschild_capture(oracle):
+    """Pins the refinement rule of the Introduction / Sec. 4 (the reading:
+    a base pixel is refined iff its class differs from an on-screen
+    4-neighbour; a child is refined iff its class differs from a 4-neighbour
+    among its 16 siblings).  With no crossing trusted (thetadot_min above any
+    |dtheta/dlambda|) N_cross = 0 everywhere, so the class is the capture
+    status, known in closed form for chi = 0.  The expected refined sets are
+    built from that closed form alone; the test also checks that an
+    8-neighbour rule, off-screen neighbours counted as different, and
+    children compared across their sibling block would each give different
+    sets, so none of those could pass."""
+    nx, ny = 26, 22
+    P = oracle.problem(metric=oracle.KERR, chi=0.0, incl=math.radians(40.0), nx=nx, ny=ny,
+                       x_min=-7.5, x_max=8.1, y_min=-7.0, y_max=6.2, levels=2,
+                       thetadot_min=1e300)
+    img = oracle.trace_image(P)
+    assert int(img["ncross"].max()) == 0
+    dx, dy = (P.x_max - P.x_min) / nx, (P.y_max - P.y_min) / ny
+    X = P.x_min + (np.arange(nx) + 0.5) * dx
+    Y = P.y_min + (np.arange(ny) + 0.5) * dy
+    XX, YY = np.meshgrid(X, Y)
+    cls, k = _schwarzschild_captured(P, XX, YY)
+    assert np.abs(k - 27.0).min() > 1e-9 * 27.0
+    assert np.array_equal(img["status"], cls)
+
+    def marked(c, diag=False, offscreen=False):
+        m = np.zeros_like(c, dtype=bool)
+        h, w = c.shape
+        nb = [(-1, 0), (1, 0), (0, -1), (0, 1)]
+        if diag:
+            nb += [(-1, -1), (-1, 1), (1, -1), (1, 1)]
+        for j in range(h):
+            for i in range(w):
+                for dj, di in nb:
+                    jj, ii = j + dj, i + di
+                    if 0 <= jj < h and 0 <= ii < w:
+                        m[j, i] |= c[jj, ii] != c[j, i]
+                    elif offscreen:
+                        m[j, i] = True
+        return m
+
+    exp0 = marked(cls)
+    assert exp0.any()
+    assert not np.array_equal(exp0, marked(cls, diag=True))
+    assert not np.array_equal(exp0, marked(cls, offscreen=True))
+    keys = img["keys"].astype(np.uint64)
+    lev = (keys >> np.uint64(12)) & np.uint64(0xF)
+    base = (keys >> np.uint64(16)).astype(np.int64)
+    got0 = np.zeros(nx * ny, dtype=bool)
+    got0[np.unique(base[lev == 1])] = True
+    assert np.array_equal(got0.reshape(ny, nx), exp0)
+    # every refined base pixel has all 16 children at level 1
+    assert int((lev == 1).sum()) == 16 * int(exp0.sum())
+
+    # level 1 -> 2: children at (k + 1/2)/4 - 1/2 of the parent width
+    offs = (np.arange(4) + 0.5) / 4.0 - 0.5
+    exp1, cross_block = set(), set()
+    blocks = {}
+    for j, i in np.argwhere(exp0):
+        cx = X[i] + offs[None, :] * dx
+        cy = Y[j] + offs[:, None] * dy
+        c, kk = _schwarzschild_captured(P, np.broadcast_to(cx, (4, 4)), np.broadcast_to(cy, (4, 4)))
+        assert np.abs(kk - 27.0).min() > 1e-9 * 27.0
+        blocks[(j, i)] = c
+        for r, q in np.argwhere(marked(c)):
+            exp1.add((int(j) * nx + int(i), int(r) * 4 + int(q)))
+    # the same children compared with neighbours outside their 4x4 block
+    fine = np.full((ny * 4, nx * 4), -1, dtype=np.int64)
+    for (j, i), c in blocks.items():
+        fine[4 * j:4 * j + 4, 4 * i:4 * i + 4] = c
+    for (j, i) in blocks:
+        for r in range(4):
+            for q in range(4):
+                y, x = 4 * j + r, 4 * i + q
+                for dy_, dx_ in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                    yy, xx = y + dy_, x + dx_
+                    if 0 <= yy < fine.shape[0] and 0 <= xx < fine.shape[1] and \
+                            fine[yy, xx] >= 0 and fine[yy, xx] != fine[y, x]:
+                        cross_block.add((int(j) * nx + int(i), r * 4 + q))
+    assert exp1 and cross_block != exp1
+    got1 = {(int(b), int((kk >> np.uint64(8)) & np.uint64(0xF)))
+            for b, kk in zip(base[lev == 2], keys[lev == 2])}
+    assert got1 == exp1
+    assert int((lev == 2).sum()) == 16 * len(exp1)
