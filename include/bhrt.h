@@ -414,12 +414,18 @@ bh_status bh_visibilities_fp64(const float* I, const bh_camera* cam, const doubl
  * (Eq. 92) summed in FP64 from the image (not from the split evaluation);
  * an image of zero flux gives inf or NaN there.
  * Modes 1-2 need nx <= 4096 and bh_visibilities_workspace_size bytes of
- * 256-byte aligned workspace; a stalled pipeline wait (bounded) sets
- * BH_ERR_TIMEOUT in the workspace status word (bh_workspace_status). */
+ * 256-byte aligned workspace.  time_budget_s >= 0 is a device time budget
+ * for modes 1-2 (0 = none): each CTA checks it before each reduction
+ * chunk issues its copies and products, and once it is spent stops there,
+ * waits for the work it has issued and sets BH_ERR_TIMEOUT in the
+ * workspace status word (read with bh_workspace_status after
+ * synchronising); V is then incomplete.  A pipeline wait that has not
+ * completed after 2 s of device time sets the same status. */
 bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes);
 bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
                           int32_t mode, double image_max, double* V, double* Vnorm,
-                          void* workspace, size_t workspace_bytes, void* stream);
+                          double time_budget_s, void* workspace, size_t workspace_bytes,
+                          void* stream);
 
 /* Fourier-domain summaries of Sec. 6.4 at n_q radii q[j] (device doubles,
  * cycles per M): V_avg[j], the normalised amplitude |V|/|V(0,0)| (Eq. 109)

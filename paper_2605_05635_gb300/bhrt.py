@@ -257,8 +257,8 @@ def lib():
                                            C.c_void_p, C.c_void_p]
         L.bh_visibilities_workspace_size.argtypes = [P(_Camera), P(C.c_size_t)]
         L.bh_visibilities.argtypes = [C.c_void_p, P(_Camera), C.c_void_p, C.c_int64, C.c_int32,
-                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
-                                      C.c_void_p]
+                                      C.c_double, C.c_void_p, C.c_void_p, C.c_double,
+                                      C.c_void_p, C.c_size_t, C.c_void_p]
         L.bh_visibility_curves_workspace_size.argtypes = [P(_Camera), C.c_int32, C.c_int32,
                                                           P(C.c_size_t)]
         L.bh_visibility_curves.argtypes = [C.c_void_p, P(_Camera), C.c_int32, C.c_void_p,
@@ -613,9 +613,17 @@ def visibilities_fp64(I: torch.Tensor, cam: Camera, uv: torch.Tensor, stream=Non
 VIS_FP64, VIS_BF16, VIS_FP16 = 0, 1, 2
 
 
+def visibilities_workspace(cam: Camera, device=None) -> torch.Tensor:
+    """A device workspace for bh_visibilities on this screen."""
+    nb = C.c_size_t(0)
+    _check(lib().bh_visibilities_workspace_size(C.byref(cam._c()), C.byref(nb)),
+           "bh_visibilities_workspace_size")
+    return _aligned_workspace(nb.value, _need_cuda(device))
+
+
 def visibilities(I: torch.Tensor, cam: Camera, uv: torch.Tensor, mode: int = VIS_BF16,
                  image_max: Optional[float] = None, stream=None, out=None, workspace=None,
-                 check: bool = True, normalised: bool = False):
+                 check: bool = True, normalised: bool = False, time_budget_s: float = 0.0):
     """Eq. (108) on the tensor cores (split BF16 / FP16) or by the FP64 direct
     sum (mode 0); returns a complex128 device tensor, or with ``normalised``
     the pair (V, |V|/|V(0,0)|) of Eqs. (108)-(109)."""
@@ -636,7 +644,8 @@ def visibilities(I: torch.Tensor, cam: Camera, uv: torch.Tensor, mode: int = VIS
                                  C.c_void_p(uv.data_ptr()), K, mode, image_max,
                                  C.c_void_p(out.data_ptr()),
                                  C.c_void_p(vn.data_ptr() if vn is not None else 0),
-                                 C.c_void_p(workspace.data_ptr()), workspace.numel(), sp),
+                                 float(time_budget_s), C.c_void_p(workspace.data_ptr()),
+                                 workspace.numel(), sp),
            "bh_visibilities")
     if check and mode != VIS_FP64:
         _check(lib().bh_workspace_status(C.c_void_p(workspace.data_ptr()), sp), "device status")

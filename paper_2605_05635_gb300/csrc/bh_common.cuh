@@ -306,10 +306,30 @@ __device__ __forceinline__ void lapse(const MetricConsts<T>& m, T R, T iR, T& H,
 // theta may leave (0, pi) inside a step (the equations continue through
 // the polar axis; the accepted state is reflected back by the caller).
 // Also returns W = 2 Sigma H and P^2/Delta for the null-constraint monitor.
+// The ray's constants of motion E = -p_T, ell = p_phi (Eq. 48) with the
+// products of them and the spin that the right-hand side uses, formed once
+// per ray or step rather than in each of its evaluations.
+template <class T>
+struct RayC {
+  T E, ell;
+  T cE, cl, c2E, E4;  // chi E, chi ell, chi^2 E, 4 E
+};
+template <class T>
+__device__ __forceinline__ RayC<T> ray_consts(const MetricConsts<T>& m, T E, T ell) {
+  RayC<T> k;
+  k.E = E;
+  k.ell = ell;
+  k.cE = m.chi * E;
+  k.cl = m.chi * ell;
+  k.c2E = m.chi2 * E;
+  k.E4 = T(4) * E;
+  return k;
+}
+
 // geo_rhs_sc takes sin(theta) and cos(theta) instead of theta.
 template <class T>
-__device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, T E, T ell, T R, T s, T c,
-                                           T pR, T pth, T d[6], T& W, T& P2oD) {
+__device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, const RayC<T>& k, T R, T s,
+                                           T c, T pR, T pth, T d[6], T& W, T& P2oD) {
   T R2 = R * R;
   T Sig = R2 + m.chi2 * c * c;               // Eq. (23)
   // the lapse needs 1/R before Delta exists: 1/R and 1/Sigma from one
@@ -323,17 +343,17 @@ __device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, T E, T ell,
   T iDs = d_rcp(Dl * s);
   T iD = s * iDs, is = Dl * iDs;
   T r2a2 = R2 + m.chi2;
-  T P = r2a2 * E - m.chi * ell;
-  T Q = ell * is - m.chi * E * s;
+  T P = r2a2 * k.E - k.cl;
+  T Q = k.ell * is - k.cE * s;
   T PoD = P * iD;
   P2oD = P * PoD;
   W = Dl * pR * pR - P2oD + pth * pth + Q * Q;
-  d[0] = (r2a2 * PoD + m.chi * (ell - m.chi * E * s * s)) * iS;   // Eq. (57)
+  d[0] = (r2a2 * PoD + (k.cl - k.c2E * (s * s))) * iS;           // Eq. (57)
   d[1] = Dl * pR * iS;                                            // Eq. (59)
   d[2] = pth * iS;                                                // Eq. (60)
-  d[3] = (m.chi * PoD + ell * is * is - m.chi * E) * iS;          // Eq. (58)
-  T dW_R = dDl * pR * pR - T(4) * R * E * PoD + PoD * PoD * dDl;  // d(W)/dR
-  T dQ = -ell * c * is * is - m.chi * E * c;                       // dQ/dth
+  d[3] = (m.chi * PoD + k.ell * is * is - k.cE) * iS;             // Eq. (58)
+  T dW_R = dDl * pR * pR - k.E4 * R * PoD + PoD * PoD * dDl;      // d(W)/dR
+  T dQ = -k.ell * c * is * is - k.cE * c;                          // dQ/dth
   T iS2 = iS * iS;
   d[4] = T(-0.5) * dW_R * iS + W * R * iS2;                       // Eq. (61)
   d[5] = -Q * dQ * iS - W * m.chi2 * s * c * iS2;                 // Eq. (62)
@@ -344,7 +364,7 @@ __device__ __forceinline__ bool geo_rhs(const MetricConsts<T>& m, T E, T ell, T 
                                         T pth, T d[6], T& W, T& P2oD) {
   T s, c;
   d_sincos(th, &s, &c);
-  return geo_rhs_sc(m, E, ell, R, s, c, pR, pth, d, W, P2oD);
+  return geo_rhs_sc(m, ray_consts(m, E, ell), R, s, c, pR, pth, d, W, P2oD);
 }
 
 // Screen position of a cell from its key (bit-exact cell-centred

@@ -498,6 +498,7 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   // derivative g^3 j depends on the state only (kI, sums s5I and seI)
   const bool vol = kVol && ip.volumetric != 0;
   double kI = kVol ? r.fI : 0.0, s5I = 0.0, seI = 0.0;
+  const RayC<double> kc = ray_consts(m, r.E, r.ell);
 #pragma unroll 1
   for (int j = 0; j < 7; ++j) {
     // zero coefficients (about a third of the triangular sums) are skipped
@@ -532,7 +533,9 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     double ys[4];
 #pragma unroll
     for (int x = 0; x < 4; ++x) ys[x] = r.y[kQC(x)] + h * q[0][x];
-    bool ok = geo_rhs(m, r.E, r.ell, ys[0], ys[1], ys[2], ys[3], k, W, P2oD);
+    double sth, cth;
+    d_sincos(ys[1], &sth, &cth);
+    bool ok = geo_rhs_sc(m, kc, ys[0], sth, cth, ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
     if (vol) kI = vol_source64(ip, m, r.E, r.ell, ys[0], ys[1]);
 #pragma unroll
@@ -716,7 +719,7 @@ static __device__ __noinline__ void project_invariants(MetricConsts<double> m, d
 // photon orbit, where the remaining time near the orbit no longer magnifies
 // a position error.  Evaluated in FP32 from truncated operands (it only
 // decides where the FP32 steps resume).
-constexpr float kDemoteKappa = 16.f;
+constexpr float kDemoteKappa = 4.f;
 static __device__ __noinline__ bool past_double_root(const ImgParams& ip, double E, double ell,
                                                      double R, double pR) {
   const MetricConsts<float> m = metric_consts<float>(ip);

@@ -56,7 +56,7 @@ static __device__ __noinline__ RhsF rhs_f32(MetricConsts<float> m, float E, floa
   RhsF o;
   float s, c;
   d_sincos2(th, thl, &s, &c);
-  geo_rhs_sc(m, E, ell, R, s, c, pR, pth, o.d, o.W, o.P2);
+  geo_rhs_sc(m, ray_consts(m, E, ell), R, s, c, pR, pth, o.d, o.W, o.P2);
   return o;
 }
 __device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, float E, float ell,
@@ -407,6 +407,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   float W = 0.f, P2oD = 1.f;
   const bool vol = kVol && ip.volumetric;
   float kI = kVol ? r.fI : 0.f, s5I = 0.f, seI = 0.f;
+  const RayC<float> kc = ray_consts(mf, r.Ef, r.ellf);
 #pragma unroll 1
   for (int j = 0; j < 7; ++j) {
     // all coefficients, zeros included: branching around the zero terms
@@ -436,7 +437,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
     // sin and cos of theta from the pair (state hi, state lo + stage offset)
     float sth, cth;
     d_sincos2(r.yh[2], r.yl[2] + h * q[0][1], &sth, &cth);
-    bool ok = geo_rhs_sc(mf, r.Ef, r.ellf, ys[0], sth, cth, ys[2], ys[3], k, W, P2oD);
+    bool ok = geo_rhs_sc(mf, kc, ys[0], sth, cth, ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
     // the source depends on the state only, so its stage-input sum is not needed
     if (vol)

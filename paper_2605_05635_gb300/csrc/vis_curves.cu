@@ -97,8 +97,8 @@ bh_status bh_visibility_curves(const float* I, const bh_camera* cam, int32_t n_q
   // path's own checks (a call with no baselines enqueues nothing), its
   // baseline-count limit and the FP64 path's row limit (2 nx doubles of
   // shared memory within 200 KiB)
-  s = bh_visibilities(I, cam, nullptr, 0, mode, image_max, nullptr, nullptr, workspace, vis,
-                      stream);
+  s = bh_visibilities(I, cam, nullptr, 0, mode, image_max, nullptr, nullptr, 0.0, workspace,
+                      vis, stream);
   if (s != BH_OK) return s;
   if (K > 0x7fffffff || (mode == 0 && (size_t)cam->nx * 2 * sizeof(double) > 200 * 1024))
     return BH_ERR_INVALID_ARG;
@@ -112,7 +112,7 @@ bh_status bh_visibility_curves(const float* I, const bh_camera* cam, int32_t n_q
   int64_t blocks = std::min<int64_t>((K + 255) / 256, (int64_t)sms * 8);
   curve_uv_kernel<<<(int)blocks, 256, 0, cs>>>(q, n_q, n_phi, uv);
   if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
-  s = bh_visibilities(I, cam, uv, K, mode, image_max, V, nullptr, ws, vis, stream);
+  s = bh_visibilities(I, cam, uv, K, mode, image_max, V, nullptr, 0.0, ws, vis, stream);
   if (s != BH_OK) return s;
   if (n_q == 0) return BH_OK;
   blocks = std::min<int64_t>(((int64_t)n_q * 32 + 255) / 256, (int64_t)sms * 8);

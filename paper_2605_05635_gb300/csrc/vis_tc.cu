@@ -46,7 +46,17 @@ constexpr int kVisMaxNx = 4096;    // bound of the per-CTA phase table
 constexpr int kSeg = 16;            // columns per thread between sincospif reseeds
 constexpr int kVisSmem = kStages * kStage + 1024 + 256 + 2048 +
                          kVisUV * (kVisMaxNx / kVisKC) * 4;
-constexpr unsigned kSpinLimit = 1u << 26;
+// A pipeline wait that has not completed after this long (device clock)
+// is treated as a stalled pipeline.
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// Leading 256 bytes of the visibility workspace.
+struct VisHdr {
+  int status;                   // bh_status of the device work
+  int reserved;
+  unsigned long long t_start;   // %globaltimer when the call's work began (ns)
+  unsigned long long budget_ns; // 0 = no budget
+};
 
 struct VisArgs {
   const double* uv;   // [K][2]
@@ -56,8 +66,20 @@ struct VisArgs {
   double scale;       // image scale applied before splitting (undone at the end)
   int fp16;           // 0: BF16 operands, 1: FP16 operands
   double* V;          // [K][2]
-  int* status;        // device status word (spin-limit exceeded)
+  VisHdr* hdr;        // status word, start time and budget
 };
+
+__device__ __forceinline__ unsigned long long vis_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void vis_begin(VisHdr* h, unsigned long long budget_ns) {
+  h->status = 0;
+  h->t_start = vis_clock();
+  h->budget_ns = budget_ns;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -73,10 +95,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-// Bounded wait on an mbarrier phase; returns false if the limit ran out.
+// Wait on an mbarrier phase, bounded by kWaitNs of device time; returns
+// false if the bound ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
+  unsigned long long t0 = 0;
+  for (unsigned it = 0;; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -85,8 +109,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255u) == 0u) {
+      const unsigned long long now = vis_clock();
+      if (it == 0) t0 = now;
+      else if (now - t0 > kWaitNs) return false;
+    }
   }
-  return false;
 }
 
 // Shared-memory matrix descriptor for tcgen05.mma: K-major operand in the
@@ -226,8 +254,11 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   const int chunks = nblk;
   const int passes = (a.ny + kVisNP - 1) / kVisNP;
   const uint32_t idesc = instr_desc(fp16);
+  const unsigned long long t_start = a.hdr->t_start, budget = a.hdr->budget_ns;
   bool ok = true;
-  unsigned use[kStages] = {0, 0};         // completed uses per stage (for parity)
+  // per stage (thread 0): TMA copies issued and waited for, MMA batches
+  // committed; the phase parities follow from these counts
+  unsigned tmas[kStages] = {0, 0}, tma_done[kStages] = {0, 0}, commits[kStages] = {0, 0};
   // epilogue accumulators for the thread's (row, column-half): P = sum c D, Q = sum s D
   float accP = 0.f, accQ = 0.f;
   const int erow = (warp & 3) * 32 + lane;          // TMEM lane this thread reads
@@ -245,14 +276,20 @@ __global__ void __launch_bounds__(kVisThreads, 1)
       unsigned char* sAl = sAh + kATile;
       unsigned char* sBh = sAl + kATile;
       unsigned char* sBl = sBh + kBTile;
-      // wait (one thread, bounded) for the MMAs that last used this stage
-      if (tid == 0 && use[s] > 0 && !mbar_wait(&bar_mma[s], (use[s] - 1) & 1)) *fail = 1;
+      // wait (one thread, bounded) for the MMAs that last used this stage;
+      // then the time budget, checked before this chunk issues any copy or
+      // product, so that a CTA stopping here leaves only committed MMAs
+      if (tid == 0) {
+        if (commits[s] > 0 && !mbar_wait(&bar_mma[s], (commits[s] - 1) & 1)) *fail = 1;
+        if (budget && vis_clock() - t_start > budget) *fail = 2;
+      }
       __syncthreads();
       if (*fail) {
         ok = false;
         break;
       }
       if (tid == 0) {
+        tmas[s]++;
         mbar_expect_tx(&bar_full[s], 2 * kBTile);
         tma_load_2d(sBh, &bmap, c * kVisKC, pass * kVisNP, &bar_full[s]);
         tma_load_2d(sBl, &bmap, a.nxp + c * kVisKC, pass * kVisNP, &bar_full[s]);
@@ -306,9 +343,10 @@ __global__ void __launch_bounds__(kVisThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
-        if (!mbar_wait(&bar_full[s], use[s] & 1)) {
+        if (!mbar_wait(&bar_full[s], (tmas[s] - 1) & 1)) {
           *fail = 1;
         } else {
+          tma_done[s] = tmas[s];
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh),
                          bl = smem_u32(sBl);
@@ -322,16 +360,16 @@ __global__ void __launch_bounds__(kVisThreads, 1)
             mma_f16(tmem, dal, dbh, idesc, true);               // lo x hi
           }
           mma_commit(&bar_mma[s]);
+          commits[s]++;
         }
       }
-      use[s]++;
       __syncthreads();
       if (*fail) ok = false;
     }
     if (!ok) break;
     // all MMAs of this pass: wait for the last commit (MMAs complete in order)
     const int last = (pass * chunks + chunks - 1) % kStages;
-    if (tid == 0 && !mbar_wait(&bar_mma[last], (use[last] - 1) & 1)) *fail = 1;
+    if (tid == 0 && !mbar_wait(&bar_mma[last], (commits[last] - 1) & 1)) *fail = 1;
     __syncthreads();
     if (*fail) {
       ok = false;
@@ -390,10 +428,13 @@ __global__ void __launch_bounds__(kVisThreads, 1)
     }
   }
   if (!ok && tid == 0) {
-    atomicCAS(a.status, 0, (int)BH_ERR_TIMEOUT);
-    // let any MMAs still in flight finish (bounded) before freeing TMEM
-    for (int s = 0; s < kStages; ++s)
-      if (use[s] > 0) mbar_wait(&bar_mma[s], (use[s] - 1) & 1);
+    atomicCAS(&a.hdr->status, 0, (int)BH_ERR_TIMEOUT);
+    // let copies and MMAs still in flight finish (bounded) before the CTA
+    // frees its tensor memory and exits
+    for (int s = 0; s < kStages; ++s) {
+      if (tmas[s] > tma_done[s]) mbar_wait(&bar_full[s], (tmas[s] - 1) & 1);
+      if (commits[s] > 0) mbar_wait(&bar_mma[s], (commits[s] - 1) & 1);
+    }
   }
   __syncthreads();
   if (warp == 0) {
@@ -463,15 +504,15 @@ extern "C" {
 bh_status bh_visibilities_workspace_size(const bh_camera* cam, size_t* bytes) {
   if (!cam || !bytes || cam->nx < 1 || cam->ny < 1) return BH_ERR_INVALID_ARG;
   int64_t nxp = ((int64_t)cam->nx + kVisKC - 1) / kVisKC * kVisKC;
-  *bytes = a256(sizeof(int)) + a256((size_t)cam->ny * 2 * nxp * 2);
+  *bytes = a256(sizeof(VisHdr)) + a256((size_t)cam->ny * 2 * nxp * 2);
   return BH_OK;
 }
 
 namespace {
 
 bh_status vis_contraction(const float* I, const bh_camera* cam, const double* uv, int64_t K,
-                          int32_t mode, double image_max, double* V, void* workspace,
-                          size_t workspace_bytes, void* stream) {
+                          int32_t mode, double image_max, double* V, double time_budget_s,
+                          void* workspace, size_t workspace_bytes, void* stream) {
   if (mode == 0) return bh_visibilities_fp64(I, cam, uv, K, V, stream);
   if (K == 0) return BH_OK;
   size_t need;
@@ -494,8 +535,8 @@ bh_status vis_contraction(const float* I, const bh_camera* cam, const double* uv
   a.fp16 = mode == 2;
   a.V = V;
   char* ws = static_cast<char*>(workspace);
-  a.status = reinterpret_cast<int*>(ws);
-  uint16_t* Bp = reinterpret_cast<uint16_t*>(ws + a256(sizeof(int)));
+  a.hdr = reinterpret_cast<VisHdr*>(ws);
+  uint16_t* Bp = reinterpret_cast<uint16_t*>(ws + a256(sizeof(VisHdr)));
   // TMA map of B2: [ny rows][2 nxp] 16-bit, box 64 x 256, 128-byte swizzle
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
@@ -509,7 +550,7 @@ bh_status vis_contraction(const float* I, const bh_camera* cam, const double* uv
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return BH_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return BH_ERR_CUDA;
+  vis_begin<<<1, 1, 0, s>>>(a.hdr, (unsigned long long)(time_budget_s * 1e9));
   vis_prepare_image<<<1216, 256, 0, s>>>(I, a, Bp);
   if (cudaFuncSetAttribute(vis_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kVisSmem) != cudaSuccess)
@@ -524,14 +565,16 @@ bh_status vis_contraction(const float* I, const bh_camera* cam, const double* uv
 
 bh_status bh_visibilities(const float* I, const bh_camera* cam, const double* uv, int64_t K,
                           int32_t mode, double image_max, double* V, double* Vnorm,
-                          void* workspace, size_t workspace_bytes, void* stream) {
+                          double time_budget_s, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  if (!(time_budget_s >= 0.0) || !std::isfinite(time_budget_s)) return BH_ERR_INVALID_ARG;
   if (!I || !cam || K < 0 || (K > 0 && (!uv || !V)) || cam->nx < 1 || cam->ny < 1 ||
       (mode != 0 && mode != 1 && mode != 2) || (mode != 0 && cam->nx > kVisMaxNx) ||
       !(cam->x_max > cam->x_min) || !(cam->y_max > cam->y_min) || !(image_max > 0.0) ||
       !std::isfinite(image_max))
     return BH_ERR_INVALID_ARG;
-  bh_status st = vis_contraction(I, cam, uv, K, mode, image_max, V, workspace, workspace_bytes,
-                                 stream);
+  bh_status st = vis_contraction(I, cam, uv, K, mode, image_max, V, time_budget_s, workspace,
+                                 workspace_bytes, stream);
   if (st != BH_OK || !Vnorm || K == 0) return st;
   const double dA = ((cam->x_max - cam->x_min) / cam->nx) * ((cam->y_max - cam->y_min) / cam->ny);
   vis_norm_kernel<<<1, kNormThreads, 0, static_cast<cudaStream_t>(stream)>>>(

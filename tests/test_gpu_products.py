@@ -163,3 +163,27 @@ def test_normalised_amplitudes_match_oracle(B, oracle, mode, tol):
         assert got.shape == (100,)
         assert np.max(np.abs(got - want)) <= tol, (name, mode)
         assert abs(got[0] - 1.0) <= tol
+
+
+def test_visibilities_time_budget_stops_cleanly(B):
+    """A device time budget already spent when the contraction starts: every
+    CTA stops at its first chunk, before issuing any copy or product, and the
+    workspace status reads BH_ERR_TIMEOUT (no fault, no hang).  The same
+    workspace then serves an unbudgeted call whose visibilities match the
+    FP64 direct mode, so the context is still usable."""
+    import torch
+    from paper_2605_05635_gb300 import workloads
+    n = 1024
+    I = torch.from_numpy(_ring(n, 12.0, r0=4.5, w=0.3)).cuda()
+    cam = B.Camera(nx=n, ny=n, x_min=-12.0, x_max=12.0, y_min=-12.0, y_max=12.0)
+    uv = torch.from_numpy(np.concatenate([[[0.0, 0.0]], workloads.uv_points(4095, seed=9)]))
+    ws = B.visibilities_workspace(cam, I.device)
+    with pytest.raises(B.BHRTError) as err:
+        B.visibilities(I, cam, uv, mode=1, workspace=ws, time_budget_s=1e-9)
+    assert err.value.code == 6  # BH_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    Vt = B.visibilities(I, cam, uv, mode=1, workspace=ws).cpu().numpy()
+    Vd = B.visibilities_fp64(I, cam, uv).cpu().numpy()
+    assert np.max(np.abs(Vt - Vd)) / abs(Vd[0]) <= 2e-4
+    with pytest.raises(B.BHRTError):
+        B.visibilities(I, cam, uv, mode=1, workspace=ws, time_budget_s=-1.0)
