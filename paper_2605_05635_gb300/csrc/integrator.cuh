@@ -357,7 +357,25 @@ struct Ray64 {
   float hdrift;
   int32_t nacc, nrej, steps;
   bool rejected;
+  bool xpend;      // a crossing of this ray is parked in its XPend slot
 };
+
+// An equatorial crossing whose evaluation is deferred: the end points, the
+// h f terms and the dense-output term of the accepted step that brackets
+// it, everything handle_crossing reads.  A persistent FP64 warp evaluates
+// parked crossings together (see trace_fp64_kernel) instead of running the
+// crossing code for one or two lanes at a time.
+struct XPend {
+  double y0[6], y1[6], hf0[6], hf1[6], hd[6];
+  double lam, h;
+};
+
+// Evaluates a parked crossing into the ray's event state.
+static __device__ __noinline__ void flush_crossing(const ImgParams& ip, MetricConsts<double> m,
+                                                   double E, double ell, const XPend& x,
+                                                   CrossState& cs, const CrossOut& co) {
+  handle_crossing(ip, m, E, ell, x.y0, x.y1, x.hf0, x.hf1, x.hd, x.lam, x.h, cs, co);
+}
 
 // Launch (Sec. 3.2): p^mu = u_o + n^(a) e_(a) with E_loc = 1 (Eq. 73),
 // lowered with g_{mu nu} (Eq. 74).  With g_Tphi + omega g_phph = 0 this gives
@@ -411,6 +429,7 @@ __device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricCons
   r.cs.ncross = 0;
   r.cs.I[0] = r.cs.I[1] = r.cs.I[2] = r.cs.I[3] = 0.0;
   r.rejected = false;
+  r.xpend = false;
   r.nacc = r.nrej = r.steps = 0;
   r.hdrift = 0.f;
 }
@@ -472,10 +491,13 @@ __device__ __forceinline__ float err_term(double y0, double y1, double he, float
 
 // kVol: the build that can integrate the volumetric intensity (Eq. 88) as a
 // seventh component; the thin-disk build carries none of its registers.
-template <bool kVol>
+// kDefer: a crossing is parked in *xp (the lane's slot) for the warp to
+// evaluate later; a crossing already parked there is evaluated first, so a
+// ray's crossings are always evaluated in order.
+template <bool kVol, bool kDefer = false>
 __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConsts<double>& m,
                                           Ray64& r, const TraceArgs& a, int64_t item,
-                                          uint32_t img) {
+                                          uint32_t img, XPend* xp = nullptr) {
   const double h = r.h;
   // rolled stage loop (see DPRolled): k is the latest stage derivative, q[u]
   // the running input sums of the next stages, s5/se/sd the running sums of
@@ -579,15 +601,34 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
         hf0[i] = h * r.f[i];
         hf1[i] = h * k[i];
       }
-      // copies: the ray state must not have its address taken (it would be
-      // demoted from registers to local memory for every step)
-      double y0c[6];
+      if (kDefer) {
+        if (r.xpend) {
+          CrossState cs = r.cs;
+          flush_crossing(ip, m, r.E, r.ell, *xp, cs, cross_out(a, item, img));
+          r.cs = cs;
+        }
 #pragma unroll
-      for (int i = 0; i < 6; ++i) y0c[i] = r.y[i];
-      CrossState cs = r.cs;
-      const CrossOut co = cross_out(a, item, img);
-      handle_crossing(ip, m, r.E, r.ell, y0c, y1, hf0, hf1, hd, r.lam, h, cs, co);
-      r.cs = cs;
+        for (int i = 0; i < 6; ++i) {
+          xp->y0[i] = r.y[i];
+          xp->y1[i] = y1[i];
+          xp->hf0[i] = hf0[i];
+          xp->hf1[i] = hf1[i];
+          xp->hd[i] = hd[i];
+        }
+        xp->lam = r.lam;
+        xp->h = h;
+        r.xpend = true;
+      } else {
+        // copies: the ray state must not have its address taken (it would be
+        // demoted from registers to local memory for every step)
+        double y0c[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y0c[i] = r.y[i];
+        CrossState cs = r.cs;
+        const CrossOut co = cross_out(a, item, img);
+        handle_crossing(ip, m, r.E, r.ell, y0c, y1, hf0, hf1, hd, r.lam, h, cs, co);
+        r.cs = cs;
+      }
     }
   }
   r.lam += h;
@@ -666,6 +707,7 @@ __device__ __forceinline__ void resume64(const ImgParams& ip, const SpillRec& s,
   r.nacc = s.nacc;
   r.nrej = s.nrej;
   r.steps = s.steps;
+  r.xpend = false;
   rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
   r.fI = ip.volumetric ? vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]) : 0.0;
 }

@@ -21,6 +21,9 @@
 
 namespace bhrt {
 
+constexpr int kTraceMaxThreads = 128;  // trace blocks are 64 or 128 threads
+constexpr int kXFlushLanes = 8;        // parked crossings evaluated together
+
 // MinBlocks = 0 leaves the register count to the compiler (2 blocks of 128
 // threads per SM); MinBlocks = 3 caps it for 3 blocks at a small spill cost.
 // The autotuner picks between them.  Vol = true is the build used when some
@@ -41,6 +44,10 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
   unsigned iter = 0;
   unsigned long long w_max = 0, w_iters = 0, w_lanes = 0;
   unsigned long long w_acc = 0, w_rej = 0, w_rays = 0, w_full = 0;
+
+  // parked crossings, one slot per thread (blocks of at most 128 threads)
+  __shared__ XPend xslot[kTraceMaxThreads];
+  XPend* const xp = &xslot[threadIdx.x];
 
   const int pass = a.source;
   if (lane == 0) mark_first(&a.hdr->t_pass[0][pass][a.level]);
@@ -86,28 +93,43 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
     }
     w_iters += 1ull;
     w_lanes += (unsigned long long)__popc(am);
+    int term = 0;
+    bool spill = false;
     if (active) {
       const int acc0 = r.nacc, rej0 = r.nrej;
-      int term = ray_step64<Vol>(*ip, m, r, a, item, img);
+      term = ray_step64<Vol, true>(*ip, m, r, a, item, img, xp);
       w_acc += (unsigned long long)(r.nacc - acc0);
       w_rej += (unsigned long long)(r.nrej - rej0);
-      if (term) {
-        finish_ray(a, item, img, term - 1, r.cs, r.hdrift, r.nacc, r.nrej, r.E, r.ell, r.lam);
-        w_rays += 1ull;
-        w_max = (unsigned long long)r.steps > w_max ? (unsigned long long)r.steps : w_max;
+      // outgoing beyond the strong-field zone, or away from the double root
+      // of its radial potential: finish in FP32
+      spill = !term && a.allow_spill && r.nacc != acc0 && r.y[4] > 0.0 &&
+              (r.y[1] > ip->demote_R ||
+               (ip->kappa > 0.0 && past_double_root(*ip, r.E, r.ell, r.y[1], r.y[4])));
+    }
+    // parked crossings: evaluated together once kXFlushLanes lanes hold one,
+    // and by a lane whose ray leaves this pass now
+    {
+      const bool mine = active && r.xpend;
+      const unsigned pm = __ballot_sync(kFull, mine);
+      if (mine && (__popc(pm) >= kXFlushLanes || term || spill)) {
+        CrossState cs = r.cs;
+        flush_crossing(*ip, m, r.E, r.ell, *xp, cs, cross_out(a, item, img));
+        r.cs = cs;
+        r.xpend = false;
+      }
+    }
+    if (term) {
+      finish_ray(a, item, img, term - 1, r.cs, r.hdrift, r.nacc, r.nrej, r.E, r.ell, r.lam);
+      w_rays += 1ull;
+      w_max = (unsigned long long)r.steps > w_max ? (unsigned long long)r.steps : w_max;
+      active = false;
+    } else if (spill) {
+      unsigned long long slot = atomicAdd(a.spill_out_count, 1ull);
+      if (slot < (unsigned long long)a.spill_cap) {
+        spill_from64(r, item, img, a.spill_out[slot]);
         active = false;
-      } else if (a.allow_spill && r.nacc != acc0 && r.y[4] > 0.0 &&
-                 (r.y[1] > ip->demote_R ||
-                  (ip->kappa > 0.0 && past_double_root(*ip, r.E, r.ell, r.y[1], r.y[4])))) {
-        // outgoing beyond the strong-field zone, or away from the double
-        // root of its radial potential: finish in FP32
-        unsigned long long slot = atomicAdd(a.spill_out_count, 1ull);
-        if (slot < (unsigned long long)a.spill_cap) {
-          spill_from64(r, item, img, a.spill_out[slot]);
-          active = false;
-        } else {
-          w_full += 1ull;
-        }
+      } else {
+        w_full += 1ull;
       }
     }
     if (budget && ((++iter & 255u) == 0u)) {
