@@ -37,7 +37,9 @@ constexpr int kVisRows = 128;       // accumulator lanes (64 baselines x cos/sin
 constexpr int kVisUV = 64;          // baselines per CTA
 constexpr int kVisKC = 64;          // reduction chunk (elements): 128 bytes of 16-bit
 constexpr int kVisNP = 256;         // image rows per pass (TMEM columns)
-constexpr int kVisThreads = 256;
+constexpr int kGenWarps = 8;        // warps that generate phase tiles and run the epilogue
+constexpr int kGenThreads = 32 * kGenWarps;
+constexpr int kVisThreads = kGenThreads + 32;  // + one warp for TMA and MMA issue
 constexpr int kStages = 2;
 constexpr int kATile = kVisRows * kVisKC * 2;    // 16 KB: one part (hi or lo) of A
 constexpr int kBTile = kVisNP * kVisKC * 2;      // 32 KB: one part of B
@@ -199,16 +201,64 @@ __global__ void vis_prepare_image(const float* I, VisArgs a, uint16_t* Bp) {
   }
 }
 
+// Wait on an mbarrier phase as one role of a warp-specialised CTA: gives up
+// (returns false) when another role has flagged a failure, or after kWaitNs
+// of device time, which it flags itself.
+__device__ __forceinline__ bool mbar_wait_role(uint64_t* bar, unsigned parity,
+                                               volatile int* fail) {
+  uint32_t a = smem_u32(bar);
+  unsigned long long t0 = 0;
+  for (unsigned it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63u) == 0u) {
+      if (*fail) return false;
+      const unsigned long long now = vis_clock();
+      if (it == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        *fail = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised CTA: warps 0..7 generate the phase tile of each chunk
+// into its pipeline stage and run the epilogue of each pass; warp 8 (one
+// lane) loads the image tiles by TMA and issues the MMAs.  Stages are handed
+// over by mbarriers (no CTA-wide barrier in the main loop):
+//   tma_full[s]  the stage's image tiles landed (expect_tx by the issuer),
+//   gen_full[s]  the 8 generator warps wrote the stage's phase tile,
+//   empty[s]     the MMAs that read the stage completed (tcgen05.commit),
+//   acc_full     all MMAs of a pass completed (the accumulators are final),
+//   acc_empty    the 8 epilogue warps read the accumulators.
+// The time budget is checked before each chunk's copies are issued; a CTA
+// that stops (budget spent, or a wait bounded by kWaitNs ran out) waits for
+// the copies and products it has issued before it frees tensor memory.
 __global__ void __launch_bounds__(kVisThreads, 1)
     vis_tc_kernel(const __grid_constant__ CUtensorMap bmap, VisArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* bar_full = reinterpret_cast<uint64_t*>(smem + kStages * kStage);  // TMA landed
-  uint64_t* bar_mma = bar_full + kStages;                  // MMAs of a stage done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_mma + kStages);
-  int* fail = reinterpret_cast<int*>(tmem_slot + 1);       // CTA-uniform failure flag
-  float* red = reinterpret_cast<float*>(tmem_slot + 4);    // epilogue exchange [2][128][2]
+  uint64_t* tma_full = reinterpret_cast<uint64_t*>(smem + kStages * kStage);
+  uint64_t* gen_full = tma_full + kStages;
+  uint64_t* empty = gen_full + kStages;
+  uint64_t* acc_full = empty + kStages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kStages * kStage + 64);
+  volatile int* fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* red = reinterpret_cast<float*>(smem + kStages * kStage + 128);  // [2][128][2]
   float* tbase = red + 512;                                // [64][nxp / 64] phase table
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -217,9 +267,12 @@ __global__ void __launch_bounds__(kVisThreads, 1)
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&bar_full[s], 1);
-      mbar_init(&bar_mma[s], 1);
+      mbar_init(&tma_full[s], 1);
+      mbar_init(&gen_full[s], kGenWarps);
+      mbar_init(&empty[s], 1);
     }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kGenWarps);
     *fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -234,66 +287,124 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
 
-  // phase generation: this thread fills rows kk (cos) and kk + 64 (sin) for
-  // baseline kk = tid % 64, columns seg * 16 .. seg * 16 + 15 of each chunk
+  // phase generation: generator thread tid fills rows kk (cos) and kk + 64
+  // (sin) for baseline kk = tid % 64, columns seg * 16 .. seg * 16 + 15 of
+  // each chunk
   const int kk = tid & 63;
-  const int seg = tid >> 6;                // 0..3
+  const int seg = (tid >> 6) & 3;          // 0..3
   const int64_t kidx = uv0 + kk;
   const double u = kidx < a.K ? a.uv[2 * kidx] : 0.0;
   const float two_u_dx = (float)(2.0 * u * a.dx);
-  float rot_s, rot_c;                      // one column step of the u-phase
-  sincospif(two_u_dx, &rot_s, &rot_c);
   // phase table: 2 u X at the first column of each chunk, reduced mod 2, in FP64
   const int nblk = a.nxp / kVisKC;
-  for (int b = seg; b < nblk; b += 4) {
-    double t = 2.0 * u * (a.x_min + (kVisKC * b + 0.5) * a.dx);
-    tbase[kk * nblk + b] = (float)(t - 2.0 * rint(0.5 * t));
+  if (tid < kGenThreads) {
+    for (int b = seg; b < nblk; b += 4) {
+      double t = 2.0 * u * (a.x_min + (kVisKC * b + 0.5) * a.dx);
+      tbase[kk * nblk + b] = (float)(t - 2.0 * rint(0.5 * t));
+    }
   }
   __syncthreads();
 
   const int chunks = nblk;
   const int passes = (a.ny + kVisNP - 1) / kVisNP;
-  const uint32_t idesc = instr_desc(fp16);
-  const unsigned long long t_start = a.hdr->t_start, budget = a.hdr->budget_ns;
-  bool ok = true;
-  // per stage (thread 0): TMA copies issued and waited for, MMA batches
-  // committed; the phase parities follow from these counts
-  unsigned tmas[kStages] = {0, 0}, tma_done[kStages] = {0, 0}, commits[kStages] = {0, 0};
+  const int total = passes * chunks;
   // epilogue accumulators for the thread's (row, column-half): P = sum c D, Q = sum s D
   float accP = 0.f, accQ = 0.f;
   const int erow = (warp & 3) * 32 + lane;          // TMEM lane this thread reads
-  const int ehalf = warp >> 2;                      // which 128-column half
-  const int64_t ek = uv0 + (erow & 63);
-  const double ev = ek < a.K ? a.uv[2 * ek + 1] : 0.0;
-  const float dv = (float)(2.0 * ev * a.dy);
-  float vrot_s, vrot_c;
-  sincospif(dv, &vrot_s, &vrot_c);
+  const int ehalf = (warp >> 2) & 1;                // which 128-column half
 
-  for (int pass = 0; pass < passes && ok; ++pass) {
-    for (int c = 0; c < chunks && ok; ++c) {
-      const int s = (pass * chunks + c) % kStages;
+  if (warp == kGenWarps) {
+    // ---------------- image tiles (TMA) and MMA issue: one lane ----------------
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(fp16);
+      const unsigned long long t_start = a.hdr->t_start, budget = a.hdr->budget_ns;
+      // per stage: TMA copies issued and waited for, MMA batches committed
+      unsigned tmas[kStages] = {0, 0}, tma_done[kStages] = {0, 0}, commits[kStages] = {0, 0};
+      auto issue_tma = [&](int g) -> bool {
+        const int s = g % kStages;
+        const unsigned use = (unsigned)(g / kStages);
+        // the stage's previous products must be done before its tiles are refilled
+        if (use > 0 && !mbar_wait_role(&empty[s], (use - 1) & 1, fail)) return false;
+        if (budget && vis_clock() - t_start > budget) {
+          *fail = 2;
+          return false;
+        }
+        unsigned char* sB = smem + s * kStage + 2 * kATile;
+        tmas[s]++;
+        mbar_expect_tx(&tma_full[s], 2 * kBTile);
+        tma_load_2d(sB, &bmap, (g % chunks) * kVisKC, (g / chunks) * kVisNP, &tma_full[s]);
+        tma_load_2d(sB + kBTile, &bmap, a.nxp + (g % chunks) * kVisKC, (g / chunks) * kVisNP,
+                    &tma_full[s]);
+        return true;
+      };
+      bool ok = issue_tma(0);
+      for (int g = 0; g < total && ok; ++g) {
+        const int s = g % kStages;
+        const unsigned use = (unsigned)(g / kStages);
+        const int pass = g / chunks, c = g % chunks;
+        if (!mbar_wait_role(&tma_full[s], use & 1, fail)) {
+          ok = false;
+          break;
+        }
+        tma_done[s] = tmas[s];
+        if (!mbar_wait_role(&gen_full[s], use & 1, fail)) {
+          ok = false;
+          break;
+        }
+        // the first products of a pass overwrite the accumulators: the
+        // previous pass's epilogue must have read them
+        if (c == 0 && pass > 0 && !mbar_wait_role(acc_empty, (pass - 1) & 1, fail)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ah = smem_u32(smem + s * kStage), al = ah + kATile;
+        const uint32_t bh = ah + 2 * kATile, bl = bh + kBTile;
+#pragma unroll
+        for (int k16 = 0; k16 < kVisKC / 16; ++k16) {
+          const uint32_t off = k16 * 32;
+          const uint64_t dah = smem_desc_sw128(ah + off), dal = smem_desc_sw128(al + off);
+          const uint64_t dbh = smem_desc_sw128(bh + off), dbl = smem_desc_sw128(bl + off);
+          mma_f16(tmem, dah, dbh, idesc, c > 0 || k16 > 0);   // hi x hi
+          mma_f16(tmem, dah, dbl, idesc, true);               // hi x lo
+          mma_f16(tmem, dal, dbh, idesc, true);               // lo x hi
+        }
+        mma_commit(&empty[s]);
+        commits[s]++;
+        if (c == chunks - 1) mma_commit(acc_full);
+        if (g + 1 < total && !issue_tma(g + 1)) ok = false;
+      }
+      if (!ok || *fail) {
+        atomicCAS(&a.hdr->status, 0, (int)BH_ERR_TIMEOUT);
+        if (!*fail) *fail = 1;
+        // let copies and products already issued finish (bounded) before
+        // the CTA frees its tensor memory and exits
+        for (int s = 0; s < kStages; ++s) {
+          if (tmas[s] > tma_done[s]) mbar_wait(&tma_full[s], (tmas[s] - 1) & 1);
+          if (commits[s] > 0) mbar_wait(&empty[s], (commits[s] - 1) & 1);
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- phase tiles and the epilogue: warps 0..7 ----------------
+    float rot_s, rot_c;                    // one column step of the u-phase
+    sincospif(two_u_dx, &rot_s, &rot_c);
+    const int64_t ek = uv0 + (erow & 63);
+    const double ev = ek < a.K ? a.uv[2 * ek + 1] : 0.0;
+    const float dv = (float)(2.0 * ev * a.dy);
+    float vrot_s, vrot_c;
+    sincospif(dv, &vrot_s, &vrot_c);
+    for (int g = 0; g < total; ++g) {
+      const int s = g % kStages;
+      const unsigned use = (unsigned)(g / kStages);
+      const int pass = g / chunks, c = g % chunks;
+      // waits are taken by every lane and decided per warp, so that a
+      // failure sends the whole warp out of the loop together
+      if (use > 0 && !__all_sync(0xffffffffu, mbar_wait_role(&empty[s], (use - 1) & 1, fail)))
+        break;
       unsigned char* sAh = smem + s * kStage;
       unsigned char* sAl = sAh + kATile;
-      unsigned char* sBh = sAl + kATile;
-      unsigned char* sBl = sBh + kBTile;
-      // wait (one thread, bounded) for the MMAs that last used this stage;
-      // then the time budget, checked before this chunk issues any copy or
-      // product, so that a CTA stopping here leaves only committed MMAs
-      if (tid == 0) {
-        if (commits[s] > 0 && !mbar_wait(&bar_mma[s], (commits[s] - 1) & 1)) *fail = 1;
-        if (budget && vis_clock() - t_start > budget) *fail = 2;
-      }
-      __syncthreads();
-      if (*fail) {
-        ok = false;
-        break;
-      }
-      if (tid == 0) {
-        tmas[s]++;
-        mbar_expect_tx(&bar_full[s], 2 * kBTile);
-        tma_load_2d(sBh, &bmap, c * kVisKC, pass * kVisNP, &bar_full[s]);
-        tma_load_2d(sBl, &bmap, a.nxp + c * kVisKC, pass * kVisNP, &bar_full[s]);
-      }
       // phase tile, hi and lo parts: a sincospif at the segment start, then
       // rotations by one column step (16 steps at most between reseeds)
       {
@@ -340,77 +451,57 @@ __global__ void __launch_bounds__(kVisThreads, 1)
           *reinterpret_cast<uint4*>(sAl + o1) = vsl;
         }
       }
+      // the writes reach the tensor cores' (async) proxy, then the warp's
+      // share of the stage is reported
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        if (!mbar_wait(&bar_full[s], (tmas[s] - 1) & 1)) {
-          *fail = 1;
-        } else {
-          tma_done[s] = tmas[s];
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh),
-                         bl = smem_u32(sBl);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&gen_full[s]);
+      if (c == chunks - 1) {
+        // epilogue of the pass: this thread reads lane erow, columns
+        // ehalf * 128 .. + 128, once all of the pass's products are done
+        if (!__all_sync(0xffffffffu, mbar_wait_role(acc_full, pass & 1, fail))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int jcol0 = pass * kVisNP + ehalf * 128;
+        for (int cb = 0; cb < 128; cb += 16) {
+          uint32_t r[16];
+          const uint32_t taddr =
+              tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ehalf * 128 + cb);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int jb = jcol0 + cb;
+          // v-phase 2 v Y_jb (mod 2) in FP64, then rotations over the 16 columns
+          const double tvp = 2.0 * ev * (a.y_min + (jb + 0.5) * a.dy);
+          float sn, cs;
+          sincospif((float)(tvp - 2.0 * rint(0.5 * tvp)), &sn, &cs);
 #pragma unroll
-          for (int k16 = 0; k16 < kVisKC / 16; ++k16) {
-            const uint32_t off = k16 * 32;
-            const uint64_t dah = smem_desc_sw128(ah + off), dal = smem_desc_sw128(al + off);
-            const uint64_t dbh = smem_desc_sw128(bh + off), dbl = smem_desc_sw128(bl + off);
-            mma_f16(tmem, dah, dbh, idesc, c > 0 || k16 > 0);   // hi x hi
-            mma_f16(tmem, dah, dbl, idesc, true);               // hi x lo
-            mma_f16(tmem, dal, dbh, idesc, true);               // lo x hi
+          for (int e = 0; e < 16; ++e) {
+            const float D = (jb + e < a.ny) ? __uint_as_float(r[e]) : 0.f;
+            accP = fmaf(cs, D, accP);
+            accQ = fmaf(sn, D, accQ);
+            const float cn = fmaf(cs, vrot_c, -sn * vrot_s);
+            sn = fmaf(sn, vrot_c, cs * vrot_s);
+            cs = cn;
           }
-          mma_commit(&bar_mma[s]);
-          commits[s]++;
         }
-      }
-      __syncthreads();
-      if (*fail) ok = false;
-    }
-    if (!ok) break;
-    // all MMAs of this pass: wait for the last commit (MMAs complete in order)
-    const int last = (pass * chunks + chunks - 1) % kStages;
-    if (tid == 0 && !mbar_wait(&bar_mma[last], (commits[last] - 1) & 1)) *fail = 1;
-    __syncthreads();
-    if (*fail) {
-      ok = false;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: this thread reads lane erow, columns ehalf * 128 .. + 128
-    const int jcol0 = pass * kVisNP + ehalf * 128;
-    for (int cb = 0; cb < 128; cb += 16) {
-      uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ehalf * 128 + cb);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-          "%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int jb = jcol0 + cb;
-      // v-phase 2 v Y_jb (mod 2) in FP64, then rotations over the 16 columns
-      const double tvp = 2.0 * ev * (a.y_min + (jb + 0.5) * a.dy);
-      float sn, cs;
-      sincospif((float)(tvp - 2.0 * rint(0.5 * tvp)), &sn, &cs);
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const float D = (jb + e < a.ny) ? __uint_as_float(r[e]) : 0.f;
-        accP = fmaf(cs, D, accP);
-        accQ = fmaf(sn, D, accQ);
-        const float cn = fmaf(cs, vrot_c, -sn * vrot_s);
-        sn = fmaf(sn, vrot_c, cs * vrot_s);
-        cs = cn;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
   }
+  __syncthreads();
+  const bool ok = *fail == 0;
   // combine: rows kk (C) and kk + 64 (S), two column halves each
-  red[ehalf * 256 + erow * 2 + 0] = accP;
-  red[ehalf * 256 + erow * 2 + 1] = accQ;
+  if (tid < kGenThreads) {
+    red[ehalf * 256 + erow * 2 + 0] = accP;
+    red[ehalf * 256 + erow * 2 + 1] = accQ;
+  }
   __syncthreads();
   if (tid < kVisUV && ok) {
     const int64_t k = uv0 + tid;
@@ -425,15 +516,6 @@ __global__ void __launch_bounds__(kVisThreads, 1)
       const double f = a.dx * a.dy / a.scale;
       a.V[2 * k] = ((double)P1 - (double)Q1) * f;
       a.V[2 * k + 1] = -((double)P2 + (double)Q2) * f;
-    }
-  }
-  if (!ok && tid == 0) {
-    atomicCAS(&a.hdr->status, 0, (int)BH_ERR_TIMEOUT);
-    // let copies and MMAs still in flight finish (bounded) before the CTA
-    // frees its tensor memory and exits
-    for (int s = 0; s < kStages; ++s) {
-      if (tmas[s] > tma_done[s]) mbar_wait(&bar_full[s], (tmas[s] - 1) & 1);
-      if (commits[s] > 0) mbar_wait(&bar_mma[s], (commits[s] - 1) & 1);
     }
   }
   __syncthreads();
