@@ -275,8 +275,6 @@ bh_status make_params(const bh_spacetime& s, const bh_camera& c, const bh_emissi
   ip.demote_R = kDemoteR;
   ip.promote_ncross = g.promote_order + 1;
   ip.kappa = g.promote_turning;
-  ip.chi_lo = (float)(s.chi - (double)(float)s.chi);
-  ip.chi2_lo = (float)(s.chi * s.chi - (double)(float)(s.chi * s.chi));
   ip.sin_o = std::sin(c.incl);
   ip.isin_o = 1.0 / ip.sin_o;
   return BH_OK;

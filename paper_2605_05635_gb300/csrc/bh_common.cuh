@@ -37,7 +37,6 @@ struct alignas(16) ImgParams {
                            // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
   double rtol, atol, thdot_min, dlam_min, promote_R, demote_R;
   double sin_o, isin_o;    // sin(theta_o) and its reciprocal (launch Carter constant)
-  float chi_lo, chi2_lo;   // chi - (float)chi and chi^2 - (float)(chi^2) (FP32 pairs)
   double kappa;            // mixed: near-double-root threshold of the radial potential
   int32_t promote_ncross;  // mixed: promote once N_cross reaches this inside demote_R
   int32_t volumetric;      // 1: intensity = Eq. (88) integral (seventh ODE component)
@@ -327,40 +326,6 @@ __device__ __forceinline__ RayC<T> ray_consts(const MetricConsts<T>& m, T E, T e
   return k;
 }
 
-// The FP32 steps' ray constants as float pairs (hi + lo), so that the FP32
-// right-hand side sees the ray's FP64 constants of motion to about 48 bits
-// rather than rounded to floats (a rounded E or ell is a neighbouring
-// geodesic, a systematic drift that no later projection undoes in position).
-struct RayCp {
-  float E, ell, cE, cl, c2E, E4;          // leading parts
-  float Elo, elllo, cElo, cllo, c2Elo, E4lo;  // low parts
-};
-// x * y for float pairs x = xh + xl, y = yh + yl, as a pair (hi, lo): the
-// product of the leading parts exactly by fmaf (Dekker's two-product) plus
-// the cross terms
-__device__ __forceinline__ void pair_mul(float xh, float xl, float yh, float yl, float& hi,
-                                         float& lo) {
-  hi = xh * yh;
-  lo = fmaf(xh, yh, -hi) + fmaf(xh, yl, xl * yh);
-}
-// From E = Eh + El, ell = lh + ll and the spin chi = m.chi + chi_lo,
-// chi^2 = m.chi2 + chi2_lo.
-__device__ __forceinline__ RayCp ray_consts_pair(const MetricConsts<float>& m, float chi_lo,
-                                                 float chi2_lo, float Eh, float El, float lh,
-                                                 float ll) {
-  RayCp k;
-  k.E = Eh;
-  k.Elo = El;
-  k.ell = lh;
-  k.elllo = ll;
-  pair_mul(m.chi, chi_lo, Eh, El, k.cE, k.cElo);
-  pair_mul(m.chi, chi_lo, lh, ll, k.cl, k.cllo);
-  pair_mul(m.chi2, chi2_lo, Eh, El, k.c2E, k.c2Elo);
-  k.E4 = 4.f * Eh;
-  k.E4lo = 4.f * El;
-  return k;
-}
-
 // geo_rhs_sc takes sin(theta) and cos(theta) instead of theta.
 template <class T>
 __device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, const RayC<T>& k, T R, T s,
@@ -394,44 +359,6 @@ __device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, const RayC<
   d[5] = -Q * dQ * iS - W * m.chi2 * s * c * iS2;                 // Eq. (62)
   return (R > T(0)) && (Dl > T(0));
 }
-// The same right-hand side in FP32 with the ray constants as float pairs:
-// the terms the constants enter (P, Q, the phi and T rates, dQ/dth and the
-// 4 R E P/Delta term of dW/dR) add their low parts.
-__device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<float>& m, const RayCp& k, float R,
-                                           float s, float c, float pR, float pth, float d[6],
-                                           float& W, float& P2oD) {
-  const float R2 = R * R;
-  const float Sig = R2 + m.chi2 * c * c;                  // Eq. (23)
-  const float iRS = d_rcp(R * Sig);
-  const float iR = Sig * iRS, iS = R * iRS;
-  float H, dH;
-  lapse(m, R, iR, H, dH);
-  const float Dl = R2 * H + m.chi2;                       // Eq. (25)
-  const float dDl = 2.f * R * H + R2 * dH;                // Eq. (35)
-  const float iDs = d_rcp(Dl * s);
-  const float iD = s * iDs, is = Dl * iDs;
-  const float r2a2 = R2 + m.chi2;
-  const float s2 = s * s, is2 = is * is;
-  const float P = (r2a2 * k.E - k.cl) + (r2a2 * k.Elo - k.cllo);
-  const float Q = (k.ell * is - k.cE * s) + (k.elllo * is - k.cElo * s);
-  const float cls = (k.cl - k.c2E * s2) + (k.cllo - k.c2Elo * s2);    // chi (ell - chi E sin^2)
-  const float lis = (k.ell * is2 - k.cE) + (k.elllo * is2 - k.cElo);  // ell / sin^2 - chi E
-  const float dQ = -(k.ell * is2 + k.cE) * c - (k.elllo * is2 + k.cElo) * c;  // dQ/dth
-  const float PoD = P * iD;
-  P2oD = P * PoD;
-  W = Dl * pR * pR - P2oD + pth * pth + Q * Q;
-  d[0] = (r2a2 * PoD + cls) * iS;                         // Eq. (57)
-  d[1] = Dl * pR * iS;                                    // Eq. (59)
-  d[2] = pth * iS;                                        // Eq. (60)
-  d[3] = (m.chi * PoD + lis) * iS;                        // Eq. (58)
-  const float RP = R * PoD;
-  const float dW_R = dDl * pR * pR - (k.E4 * RP + k.E4lo * RP) + PoD * PoD * dDl;  // d(W)/dR
-  const float iS2 = iS * iS;
-  d[4] = -0.5f * dW_R * iS + W * R * iS2;                 // Eq. (61)
-  d[5] = -Q * dQ * iS - W * m.chi2 * s * c * iS2;         // Eq. (62)
-  return (R > 0.f) && (Dl > 0.f);
-}
-
 template <class T>
 __device__ __forceinline__ bool geo_rhs(const MetricConsts<T>& m, T E, T ell, T R, T th, T pR,
                                         T pth, T d[6], T& W, T& P2oD) {

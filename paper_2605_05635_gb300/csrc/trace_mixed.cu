@@ -51,19 +51,18 @@ struct RhsF {
   float W, P2;
 };
 // theta is the pair th + thl (see d_sincos2).
-// The constants of motion are the pairs E = Eh + El, ell = lh + ll.
-static __device__ __noinline__ RhsF rhs_f32(MetricConsts<float> m, RayCp k, float R, float th,
-                                            float thl, float pR, float pth) {
+static __device__ __noinline__ RhsF rhs_f32(MetricConsts<float> m, float E, float ell, float R,
+                                            float th, float thl, float pR, float pth) {
   RhsF o;
   float s, c;
   d_sincos2(th, thl, &s, &c);
-  geo_rhs_sc(m, k, R, s, c, pR, pth, o.d, o.W, o.P2);
+  geo_rhs_sc(m, ray_consts(m, E, ell), R, s, c, pR, pth, o.d, o.W, o.P2);
   return o;
 }
-__device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, const RayCp& k,
+__device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, float E, float ell,
                                              float R, float th, float thl, float pR, float pth,
                                              float* d) {
-  const RhsF o = rhs_f32(m, k, R, th, thl, pR, pth);
+  const RhsF o = rhs_f32(m, E, ell, R, th, thl, pR, pth);
 #pragma unroll
   for (int i = 0; i < 6; ++i) d[i] = o.d[i];
 }
@@ -136,8 +135,7 @@ struct RayMx {
   float h;
   float lh, ll;        // affine parameter as hi + lo
   double E, ell;
-  float Ef, ellf;      // E and ell as float pairs (Ef + El, ellf + elll)
-  float El, elll;
+  float Ef, ellf;
   CrossState cs;
   float fI;            // volumetric source at the state (FSAL of the seventh component)
   float Ih, Il;        // volumetric intensity so far as hi + lo (cs.I[0] at hand-off)
@@ -177,8 +175,8 @@ __device__ __forceinline__ void mx_resume(const ImgParams& ip, const SpillRec& s
   df_from(s.lam, x.lh, x.ll);
   x.E = s.E;
   x.ell = s.ell;
-  df_from(s.E, x.Ef, x.El);
-  df_from(s.ell, x.ellf, x.elll);
+  x.Ef = (float)s.E;
+  x.ellf = (float)s.ell;
 #pragma unroll
   for (int i = 0; i < 4; ++i) x.cs.I[i] = s.I[i];
   x.cs.lam_last = s.lam_last;
@@ -189,8 +187,7 @@ __device__ __forceinline__ void mx_resume(const ImgParams& ip, const SpillRec& s
   x.nacc = s.nacc;
   x.nrej = s.nrej;
   x.steps = s.steps;
-  rhs_f32_into(mf, ray_consts_pair(mf, ip.chi_lo, ip.chi2_lo, x.Ef, x.El, x.ellf, x.elll),
-               x.yh[1], x.yh[2], x.yl[2], x.yh[4], x.yh[5], x.f);
+  rhs_f32_into(mf, x.Ef, x.ellf, x.yh[1], x.yh[2], x.yl[2], x.yh[4], x.yh[5], x.f);
   if (kVol) {
     df_from(s.I[0], x.Ih, x.Il);
     x.fI = ip.volumetric
@@ -250,10 +247,9 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   df_from(0.0, r.yh[3], r.yl[3]);
   df_from(ip.sq_grr * (-ip.r_obs * id), r.yh[4], r.yl[4]);
   df_from(ip.sq_gth * (-Y * id), r.yh[5], r.yl[5]);
-  df_from(r.E, r.Ef, r.El);
-  df_from(r.ell, r.ellf, r.elll);
-  const RayCp kc = ray_consts_pair(mf, ip.chi_lo, ip.chi2_lo, r.Ef, r.El, r.ellf, r.elll);
-  rhs_f32_into(mf, kc, r.yh[1], r.yh[2], r.yl[2], r.yh[4], r.yh[5], r.f);
+  r.Ef = (float)r.E;
+  r.ellf = (float)r.ell;
+  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yl[2], r.yh[4], r.yh[5], r.f);
   float d0 = 0.f, d1 = 0.f, sc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -266,7 +262,7 @@ __device__ __forceinline__ void ray_init_mx(const ImgParams& ip, const MetricCon
   d1 = sqrtf(d1 / 6.f);
   const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * __fdividef(d0, d1);
   float f1[6];
-  rhs_f32_into(mf, kc, r.yh[1] + h0 * r.f[1], r.yh[2], r.yl[2] + h0 * r.f[2],
+  rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1] + h0 * r.f[1], r.yh[2], r.yl[2] + h0 * r.f[2],
                r.yh[4] + h0 * r.f[4], r.yh[5] + h0 * r.f[5], f1);
   float d2 = 0.f;
 #pragma unroll
@@ -411,7 +407,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
   float W = 0.f, P2oD = 1.f;
   const bool vol = kVol && ip.volumetric;
   float kI = kVol ? r.fI : 0.f, s5I = 0.f, seI = 0.f;
-  const RayCp kc = ray_consts_pair(mf, ip.chi_lo, ip.chi2_lo, r.Ef, r.El, r.ellf, r.elll);
+  const RayC<float> kc = ray_consts(mf, r.Ef, r.ellf);
 #pragma unroll 1
   for (int j = 0; j < 7; ++j) {
     // all coefficients, zeros included: branching around the zero terms
@@ -526,7 +522,7 @@ __device__ __forceinline__ int ray_step_mx(const ImgParams& ip, const MetricCons
       df_from(th, r.yh[2], r.yl[2]);
       df_from(pth, r.yh[5], r.yl[5]);
       df_from(ph, r.yh[3], r.yl[3]);
-      rhs_f32_into(mf, kc, r.yh[1], r.yh[2], r.yl[2], r.yh[4], r.yh[5], r.f);
+      rhs_f32_into(mf, r.Ef, r.ellf, r.yh[1], r.yh[2], r.yl[2], r.yh[4], r.yh[5], r.f);
       if (vol)
         r.fI = vol_source32(ip, mf, r.Ef, r.ellf, r.yh[1], dtheta_eq(r.yh[2], r.yl[2], 0.f));
     }
