@@ -75,7 +75,10 @@ def test_argument_errors_return_before_device_work(B):
                                None, ws, 0, None)
     assert code == 3
     for badint in (B.Integrator(precision=7)._c(), B.Integrator(promote_order=-1)._c(),
-                   B.Integrator(promote_order=1001)._c()):
+                   B.Integrator(promote_order=1001)._c(),
+                   B.Integrator(promote_turning=-1e-3)._c(),
+                   B.Integrator(promote_turning=1.5)._c(),
+                   B.Integrator(promote_turning=float("nan"))._c()):
         code = lib.bh_trace_points(C.byref(st), C.byref(cam), C.byref(em), C.byref(badint), 0,
                                    None, None, ws, 0, None)
         assert code == 1
@@ -154,3 +157,15 @@ def test_workspace_sizes(B):
 def test_status_strings(B):
     for code in range(9):
         assert B.status_string(code)
+
+
+def test_visibility_call_validates_budget_and_mode(B):
+    """bh_visibilities refuses a negative or non-finite time budget and an
+    unknown mode before any device work (no workspace needed to see it)."""
+    lib = B.lib()
+    cam = B.Camera(nx=8, ny=8)._c()
+    dummy = C.c_void_p(256)  # never dereferenced: validation fails first
+    for budget, mode in ((-1.0, 1), (float("inf"), 1), (float("nan"), 1), (0.0, 3)):
+        code = lib.bh_visibilities(dummy, C.byref(cam), dummy, 1, mode, 1.0, dummy, None, budget,
+                                   None, 0, None)
+        assert code == 1, (budget, mode)

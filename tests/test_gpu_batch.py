@@ -131,3 +131,23 @@ def test_plan_fixed_launch_shapes_give_identical_planes(B):
         with pytest.raises(B.BHRTError):
             plan.set_launch(0, 0, 128, 0)
     plan.close()
+
+
+def test_sweep96_mixed_every_pixel_vs_fp64(B):
+    """The 96-image sweep as bench.py times it (256^2, three levels, mixed,
+    one batched plan) against single-image FP64 traces (rtol 1e-10, pinned to
+    the oracle by test_gpu_trace.py) of eight images, one per spin: every
+    pixel within 1e-4 of each image's maximum."""
+    from paper_2605_05635_gb300 import workloads
+    base = workloads.sweep_96()
+    flats = [dict(d, **workloads.MIXED_INTEG) for d in base]
+    plan = B.Plan([B.from_flat(d) for d in flats])
+    plan.launch()
+    plan.check()
+    for k in range(0, 96, 12):
+        ref = B.trace_batch([B.from_flat(dict(base[k], **workloads.FP64_INTEG))])[0]
+        a = plan.outputs[k]["I"].double()
+        b = ref["I"].double()
+        err = float(((a - b).abs() / b.abs().max()).max())
+        assert err <= 1e-4, (k, err)
+    plan.close()

@@ -110,3 +110,33 @@ def test_mixed_points_match_oracle(B, oracle):
             continue
         assert abs(g[k]["I_tot"] - r[k]["I_tot"]) <= TOL_MIXED * scale
         assert g[k]["E"] == pytest.approx(r[k]["E"], rel=1e-14)
+
+
+def test_mixed_polar_axis_rays(B, oracle):
+    """Rays with screen X near 0 have ell near 0 and pass close to the polar
+    axis, where the FP32 right-hand side needs sin(theta) to relative
+    precision near theta = pi (the angle is taken from its float pair).
+    Mixed points mode (FP32 -> FP64 -> FP32 passes) against the oracle at
+    rtol 1e-10: intensity within 1e-4 of the largest, classes exact except
+    class-sensitive rays."""
+    from paper_2605_05635_gb300 import workloads
+    flat = _mixed_flat(workloads, metric=0, chi=0.9, incl=math.radians(17.0))
+    rng = np.random.default_rng(17)
+    Y = np.concatenate([np.linspace(-8.0, -3.0, 40), np.linspace(3.0, 8.0, 24)])
+    X = rng.choice([-1.0, 1.0], Y.size) * 10.0 ** rng.uniform(-4, -1.5, Y.size)
+    xy = np.stack([X, Y], 1)
+    st, cam, em, it = B.from_flat(flat)
+    g = B.trace_points(st, cam, em, it, xy)
+    r = oracle.trace_points(oracle.problem(**{**oracle_flat(flat, oracle), "rtol": 1e-10,
+                                              "atol": 1e-12}), xy)
+    scale = float(np.max(r["I_tot"]))
+    assert scale > 0
+    compared = 0
+    for k in range(len(xy)):
+        if (g[k]["status"], g[k]["ncross"]) != (r[k]["status"], r[k]["ncross"]):
+            assert class_sensitive(oracle, flat, *xy[k]), xy[k]
+            continue
+        assert abs(g[k]["I_tot"] - r[k]["I_tot"]) <= TOL_MIXED * scale, (xy[k], g[k]["I_tot"],
+                                                                         r[k]["I_tot"])
+        compared += 1
+    assert compared >= 56
