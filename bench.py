@@ -42,9 +42,10 @@ FLOP_PER_STEP = 6 * 84 + 504
 FP64_PEAK_FLOPS = 1.25e12          # GB300 nominal FP64 vector rate
 KEYS_CAP = 1 << 23                 # refinement-pattern keys kept per image
 # DRAM bytes (read + write) per bench step of each trace kernel's launches
-# on the 512^2 six-image mixed sweep, from one ncu capture of the current
-# kernels (dram__bytes_read.sum + dram__bytes_write.sum over the kernel's
-# launches of one plan launch); to be retaken whenever a trace kernel changes
+# on the 512^2 six-image mixed thin-disk sweep, from one ncu capture of the
+# current kernels (dram__bytes_read.sum + dram__bytes_write.sum over the
+# kernel's launches of one plan launch); to be retaken whenever a trace kernel
+# changes.  Not measured for the volumetric layer, which reports null.
 TRAFFIC_PER_STEP = {"trace_fp64_kernel": 2.15e9, "trace_mixed_kernel": 2.20e9}
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
@@ -1104,7 +1105,7 @@ def main():
         r32 = kernel_roof(steps_acc, trace_ms, FP32_PEAK_FLOPS, "trace_mixed_kernel", fp32_src)
         r64 = kernel_roof(steps64, ms64, FP64_PEAK_FLOPS, "trace_fp64_kernel", fp64_src)
         for r in (r32, r64):
-            r["traffic"] = TRAFFIC_PER_STEP.get(r["kernel"])
+            r["traffic"] = None if vol else TRAFFIC_PER_STEP.get(r["kernel"])
             r["traffic_unit"] = "bytes per step (all of the kernel's launches of one step)"
         r64["promoted_rays"] = promoted
         r64["pass"] = "FP64 promoted pass of the mixed path"

@@ -493,8 +493,10 @@ __device__ __forceinline__ float err_term(double y0, double y1, double he, float
 // seventh component; the thin-disk build carries none of its registers.
 // kDefer: a crossing is parked in *xp (the lane's slot) for the warp to
 // evaluate later; a crossing already parked there is evaluated first, so a
-// ray's crossings are always evaluated in order.
-template <bool kVol, bool kDefer = false>
+// ray's crossings are always evaluated in order.  kEvents = false skips the
+// crossing events altogether (a caller that needs only the ray's fate: the
+// fate does not depend on them).
+template <bool kVol, bool kDefer = false, bool kEvents = true>
 __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConsts<double>& m,
                                           Ray64& r, const TraceArgs& a, int64_t item,
                                           uint32_t img, XPend* xp = nullptr) {
@@ -591,7 +593,7 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     r.cs.I[0] = I1;
     r.fI = kI;
   }
-  {
+  if (kEvents) {
     const double s0 = r.y[2] - kHalfPi, s1 = y1[2] - kHalfPi;
     if ((s0 > 0.0 && s1 <= 0.0) || (s0 < 0.0 && s1 >= 0.0)) {
       double hf0[6], hf1[6], hd[6];

@@ -32,7 +32,7 @@ __device__ __forceinline__ int ray_fate(const ImgParams& ip, const MetricConsts<
   Ray64 r;
   ray_init64(ip, m, X, Y, r);
   int term = 0;
-  while (term == 0) term = ray_step64<false>(ip, m, r, none, 0, 0);
+  while (term == 0) term = ray_step64<false, false, false>(ip, m, r, none, 0, 0);
   acc += (unsigned long long)r.nacc;
   rej += (unsigned long long)r.nrej;
   return term - 1;
@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(128) shadow_kernel(ShadowArgs s) {
   const ImgParams& ip = *s.ip;
   const MetricConsts<double> m = metric_consts<double>(ip);
   const unsigned long long budget = s.hdr->budget_ns, t0 = s.hdr->t_start;
-  // crossings are located but go nowhere: level >= 1 of image mode has no
-  // per-pixel transfer-map planes
+  // the rays' crossing events are not evaluated (kEvents = false); the
+  // arguments describe a level without per-pixel planes all the same
   TraceArgs none{};
   none.level = 1;
   none.mode = 0;

@@ -30,6 +30,9 @@ FP64_INTEG = dict(precision=0, rtol=1e-10, atol=1e-12, max_steps=1_000_000, cap_
 # through zero, without changing the images); rays within 3e-3 of a double
 # root of their radial potential take FP64 steps (promote_turning).
 MIXED_INTEG = dict(FP64_INTEG, precision=1, rtol=1e-8, atol=1e-8, promote_turning=3e-3)
+# The volumetric layer (Eq. 88) integrates the source along the whole path, so
+# near-critical rays need their FP64 steps from further out: kappa = 3e-2.
+VOLUMETRIC_TURNING = 3e-2
 
 
 def kerr_64():
@@ -53,6 +56,8 @@ def sweep_512(precision=0, volumetric=0):
                      ny=512, x_min=-12.0, x_max=12.0, y_min=-12.0, y_max=12.0, levels=3,
                      **HALO[metric], **EMISSION, volumetric=int(volumetric),
                      **(MIXED_INTEG if precision == 1 else FP64_INTEG))
+            if precision == 1 and volumetric:
+                d["promote_turning"] = VOLUMETRIC_TURNING
             out.append(d)
     return out
 
