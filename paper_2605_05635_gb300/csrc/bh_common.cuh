@@ -245,33 +245,88 @@ __device__ __forceinline__ double d_exp(double x) {
   return (t * p) * __longlong_as_double((long long)((ik >> 5) + 1023) << 52);
 }
 
-// FP64 log(1 + x) for x > -1 without a slow path: u = 1 + x = 2^e m with m in
-// [sqrt(1/2), sqrt(2)); log m = 2 atanh(t), t = (m - 1)/(m + 1), |t| <= 0.172,
-// by its series to t^21 (truncation below 1e-18); e ln 2 with a two-part ln 2;
-// plus the first-order correction for the rounding of 1 + x.
+// FP64 log(1 + x) for x > -1 without a slow path or a division:
+// u = 1 + x = 2^e m with m in [1, 2); the six leading fraction bits of m pick
+// j and a table factor r_j near 1/m (gen_log_table.py), so z = m r_j - 1 (one
+// fma) has |z| <= 1/64 and log u = (e + s_j) ln 2 + T_j + log(1 + z), with
+// T_j = -log r_j - s_j ln 2 as two doubles and log(1 + z) by its Taylor
+// series to z^9 (truncation below 6e-18 relative); the rounding of 1 + x is
+// corrected to first order, (x - (u - 1)) / u, with 1/u taken as r_j 2^-e.
+static __device__ const double kLogR[64] = {
+    1.0, 0.9770992366412213, 0.9624060150375939, 0.9481481481481482,
+    0.9343065693430657, 0.920863309352518, 0.9078014184397163, 0.8951048951048951,
+    0.8827586206896552, 0.8707482993197279, 0.8590604026845637, 0.847682119205298,
+    0.8366013071895425, 0.8258064516129032, 0.8152866242038217, 0.8050314465408805,
+    0.7950310559006211, 0.7852760736196319, 0.7757575757575758, 0.7664670658682635,
+    0.757396449704142, 0.7485380116959064, 0.7398843930635838, 0.7314285714285714,
+    0.7231638418079096, 0.7150837988826816, 0.7071823204419889, 0.6994535519125683,
+    0.6918918918918919, 0.6844919786096256, 0.6772486772486772, 0.6701570680628273,
+    0.6632124352331606, 0.6564102564102564, 0.649746192893401, 0.6432160804020101,
+    0.6368159203980099, 0.6305418719211823, 0.624390243902439, 0.6183574879227053,
+    0.6124401913875598, 0.6066350710900474, 0.6009389671361502, 0.5953488372093023,
+    0.5898617511520737, 0.5844748858447488, 0.579185520361991, 0.5739910313901345,
+    0.5688888888888889, 0.5638766519823789, 0.5589519650655022, 0.5541125541125541,
+    0.5493562231759657, 0.5446808510638298, 0.540084388185654, 0.5355648535564853,
+    0.5311203319502075, 0.5267489711934157, 0.5224489795918368, 0.5182186234817814,
+    0.5140562248995983, 0.5099601593625498, 0.5059288537549407, 0.5,
+};
+static __device__ const double kLogTHi[64] = {
+    0.0, 0.023167059281534418, 0.03831886430213666, 0.05324451451881224,
+    0.06795066190850778, 0.08244366921107454, 0.09672962645855114, 0.11081436634029011,
+    0.12470347850095725, 0.1384023228591192, 0.151916042025842, 0.16524957289530717,
+    0.17840765747281825, 0.19139485299962947, 0.20421554142869083, 0.2168739383006143,
+    0.2293741010648459, 0.24171993688714513, 0.25391520998096345, 0.2659635484971379,
+    0.2778684510034563, 0.2896332925830427, 0.30126133057816185, 0.3127557100038969,
+    0.324119468654212, 0.3353555419211378, 0.3464667673462086, 0.3574558889218038,
+    0.36832556115870757, 0.3790783529349695, 0.38971675114002524, 0.40024316412701266,
+    -0.28248725557467697, -0.27217788591581565, -0.2619737157415739, -0.2518726197550701,
+    -0.2418725364204867, -0.23197146543777517, -0.2221674653411543, -0.21245865121419336,
+    -0.20284319251475144, -0.19331931100349606, -0.18388527877013738, -0.17453941635189965,
+    -0.16528009093910292, -0.1561057146630616, -0.14701474296180975, -0.1380056730194437,
+    -0.12907704227514236, -0.12022742699815989, -0.11145544092532278, -0.10275973395776894,
+    -0.09413899091386191, -0.08559193033540353, -0.0771173033444312, -0.06871389254805173,
+    -0.06038051098890748, -0.0521160011390141, -0.04391923393483558, -0.03578910785158529,
+    -0.02772454801485477, -0.019724505347778573, -0.011787955752042173, 0.0,
+};
+static __device__ const double kLogTLo[64] = {
+    0.0, -3.095927552179262e-19, -2.3579961573512846e-18, 1.803871134979952e-18,
+    3.9239563038692484e-18, -4.707903082046854e-18, -4.0291867005826106e-18, 2.0511100808140527e-18,
+    -4.6522609636496624e-18, -1.3766819196398948e-17, 4.1233095848339465e-19, -9.227573884334224e-18,
+    1.2720936612962572e-17, -1.126213516780448e-17, 7.9379985298027e-18, 6.285749669211092e-18,
+    -5.684839459813236e-18, 1.323779871210866e-17, -7.180735656435798e-18, 1.35209848201012e-19,
+    2.2502748630777633e-17, 2.0535953219858177e-17, -1.5120043309967385e-17, -1.3650721793001109e-17,
+    -4.488767429940198e-18, -1.3746739934976202e-17, -3.591951952851805e-18, -2.4269548334425144e-17,
+    2.690672380132659e-17, 1.8481479367349684e-17, 2.734172667856699e-17, -1.655340963311913e-17,
+    4.5622709592656976e-18, -1.859318262481925e-17, 1.878144810277299e-17, -1.2846709260565683e-17,
+    -5.086688062206503e-18, 1.0705552511300431e-17, 1.1664564654755913e-17, 1.8248974208288598e-18,
+    9.177560001701116e-18, 2.3084535888000873e-18, -1.51192377141417e-18, -1.2294483916404324e-17,
+    1.4935930931804023e-18, 1.2806970330932863e-17, -1.6045849809178003e-18, -9.927673066865803e-18,
+    1.380833506137427e-17, -6.703429385028035e-18, 4.722382936838005e-18, 5.5749926045490845e-18,
+    1.9720664099579867e-18, 4.505830273858094e-18, -1.6980741255382134e-18, 5.131966502090055e-18,
+    1.2896019993525642e-18, -2.445091174292264e-18, -1.7623552700046253e-18, -7.2846227792942925e-19,
+    -1.6936634670586275e-19, 1.3445979863167513e-18, -2.208154666796599e-19, 0.0,
+};
 __device__ __forceinline__ double d_log1p(double x) {
   const double u = 1.0 + x;
   const long long ub = __double_as_longlong(u);
-  int e = (int)((ub >> 52) & 0x7ff) - 1023;
-  double m = __longlong_as_double((ub & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
-  if (m > 1.4142135623730951) {
-    m *= 0.5;
-    e += 1;
-  }
-  const double t = (m - 1.0) * d_rcp(m + 1.0), t2 = t * t;
-  double p = fma(t2, 0.047619047619047616, 0.05263157894736842);  // 1/21, 1/19
-  p = fma(p, t2, 0.058823529411764705);  // 1/17
-  p = fma(p, t2, 0.06666666666666667);  // 1/15
-  p = fma(p, t2, 0.07692307692307693);  // 1/13
-  p = fma(p, t2, 0.09090909090909091);  // 1/11
-  p = fma(p, t2, 0.1111111111111111);  // 1/9
-  p = fma(p, t2, 0.14285714285714285);  // 1/7
-  p = fma(p, t2, 0.2);  // 1/5
-  p = fma(p, t2, 0.3333333333333333);  // 1/3
-  const double lm = 2.0 * fma(p * t2, t, t);
-  const double corr = (x - (u - 1.0)) * d_rcp(u);
-  const double ed = (double)e;
-  return fma(ed, 0.6931471805598903, fma(ed, 5.497923018708371e-14, lm + corr));
+  const int e = (int)((ub >> 52) & 0x7ff) - 1023;
+  const int j = (int)((ub >> 46) & 63);
+  const double m = __longlong_as_double((ub & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+  const double r = __ldg(&kLogR[j]);
+  const double z = fma(m, r, -1.0);
+  double p = fma(z, 0.1111111111111111, -0.125);  // 1/9, -1/8
+  p = fma(p, z, 0.14285714285714285);   // 1/7
+  p = fma(p, z, -0.16666666666666666);  // -1/6
+  p = fma(p, z, 0.2);                   // 1/5
+  p = fma(p, z, -0.25);                 // -1/4
+  p = fma(p, z, 0.3333333333333333);    // 1/3
+  p = fma(p, z, -0.5);                  // -1/2
+  const double lz = fma(z * z, p, z);
+  const double sc = __longlong_as_double((long long)(1023 - e) << 52);  // 2^-e
+  const double corr = (x - (u - 1.0)) * (r * sc);
+  const double k = (double)(e + (j >> 5));
+  return fma(k, 0.6931471805598903,
+             __ldg(&kLogTHi[j]) + fma(k, 5.497923018708371e-14, __ldg(&kLogTLo[j]) + (lz + corr)));
 }
 
 __device__ __forceinline__ double d_pow(double a, double b) { return pow(a, b); }

@@ -885,6 +885,19 @@ __device__ __forceinline__ int64_t claim(unsigned long long* head, bool need, in
   return need ? (int64_t)base + __popc(mask & ((1u << lane) - 1u)) : -1;
 }
 
+// Whether a lane without a ray claims the next item now.  With Batch > 1 a
+// free lane waits until Batch lanes of its warp are free (or none is busy),
+// so that the divergent start of new rays (a resume or a launch with its
+// dependent global loads) runs for several lanes at once.  All lanes of the
+// warp must call it.
+template <int Batch>
+__device__ __forceinline__ bool refill_now(bool want, bool active) {
+  if (Batch <= 1) return want;
+  const unsigned wm = __ballot_sync(kFull, want);
+  const unsigned am = __ballot_sync(kFull, active);
+  return want && (__popc(wm) >= Batch || am == 0u);
+}
+
 // Pass timeline marks (WsHeader::t_pass): the first writer of a slot wins.
 __device__ __forceinline__ void mark_first(unsigned long long* slot) {
   if (*reinterpret_cast<volatile unsigned long long*>(slot) == 0ull)

@@ -10,7 +10,9 @@
 // Scheduling: a persistent grid; every warp keeps 32 rays in flight and
 // refills lanes whose ray has terminated with the next items of a global
 // queue (one warp-aggregated atomic per refill), so long near-critical rays
-// do not hold idle lanes hostage.
+// do not hold idle lanes hostage.  Free lanes refill in groups of
+// kRefillLanes: starting a ray (above all resuming a promoted one, with its
+// projection onto the launch invariants) is divergent FP64 work.
 //
 // In the all-FP64 path this kernel traces every ray.  In the mixed path it
 // is the promoted pass: it resumes rays handed over by the FP32 kernel and,
@@ -23,6 +25,7 @@ namespace bhrt {
 
 constexpr int kTraceMaxThreads = 128;  // trace blocks are 64 or 128 threads
 constexpr int kXFlushLanes = 8;        // parked crossings evaluated together
+constexpr int kRefillLanes = 4;        // free lanes that start new rays together
 
 // MinBlocks = 0 leaves the register count to the compiler (2 blocks of 128
 // threads per SM); MinBlocks = 3 caps it for 3 blocks at a small spill cost.
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
   const int pass = a.source;
   if (lane == 0) mark_first(&a.hdr->t_pass[0][pass][a.level]);
   while (true) {
-    const bool need = !active && !drained;
+    const bool need = refill_now<kRefillLanes>(!active && !drained, active);
     int64_t idx = claim(a.head, need, lane);
     if (need) {
       if (idx < n_items) {

@@ -91,6 +91,11 @@ __device__ __forceinline__ float step_factor_mx(float e, bool after_reject) {
   return fminf(fmaxf(fac, 0.2f), after_reject ? 1.f : 10.f);
 }
 
+// Free lanes that start new rays together (refill_now): a launch from the
+// screen forms the ray's constants in FP64, and a resume reads a spill
+// record, both divergent.
+constexpr int kMxRefillLanes = 16;
+
 // pi/2 as a float pair hi + lo, and pi (hi part) for the axis test.
 constexpr float kHalfPiHi = 1.57079637050628662109375f;
 constexpr float kHalfPiLo = -4.37113900018624283e-8f;
@@ -572,7 +577,7 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_mixed_kernel(TraceArgs a
   const int pass = (a.source ? 2 : 0);
   if (lane == 0) mark_first(&a.hdr->t_pass[0][pass][a.level]);
   while (true) {
-    const bool need = !active && !drained;
+    const bool need = refill_now<kMxRefillLanes>(!active && !drained, active);
     int64_t idx = claim(a.head, need, lane);
     if (need) {
       if (idx < n_items) {

@@ -10,7 +10,8 @@ Bounds, with u the unit roundoff of the format (FP32 2^-24, FP64 2^-53):
 sine and cosine within 4u absolute over the polar angle and the trial
 stages around it, [-0.6, pi + 0.6], and the sine within 8u relative next to
 the poles (1/sin(theta) enters the right-hand side); log(1 + x) within 8u
-relative on [1e-3, 1e3] (x = R / lambda_c of the cored-NFW lapse); exp (FP64)
+relative on [1e-3, 1e3] (x = R / lambda_c of the cored-NFW lapse) and, in FP64,
+on [-0.89, -1e-6] (x = R / R_in - 1 of the emissivity); exp (FP64)
 within 8u relative on [-700, 5] and 0 below -708; the reciprocal and the
 reciprocal square root (FP64) within 4u relative.
 """
@@ -126,7 +127,9 @@ def test_f64_exp_log1p_rcp(lib):
     assert np.max(np.abs(e - ref) / ref) <= 8 * U64
     _, _, _, _, e_low, _, _ = _f64(lib, np.array([-710.0, -750.0, -1e4]))
     assert np.all(e_low == 0.0)
-    xl = np.logspace(-3, 3, 3001)
+    # x = R / lambda_c of the cored-NFW lapse, and R / R_in - 1 of the
+    # emissivity (negative inside R_in)
+    xl = np.concatenate([np.logspace(-3, 3, 3001), -np.logspace(-6, -0.05, 1001)])
     x, _, _, l, _, _, _ = _f64(lib, xl)
     ref = np.array([float(Fraction(math.log1p(v))) for v in x])  # libm log1p, < 1u
     assert np.max(np.abs(l - ref) / ref) <= 8 * U64
