@@ -65,6 +65,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.thread = None
+        self.first = 0
 
     def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -80,6 +81,13 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a moment to start: wait (bounded) for its first
+        # sample, then count only the samples taken after this point, i.e.
+        # inside the timed region that follows
+        t_end = time.time() + 5.0
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -97,7 +105,7 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.first:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -430,7 +438,9 @@ def run_vis1024(args, B, workloads, dev, stream):
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
         "fp16_split": {"ms": res["fp16"]["ms"], "max_err_vs_fp64_over_V0": errs["fp16"]},
         "max_err_vs_fp64_over_V0": errs["bf16"], "fp64_sample": int(ks.numel()),
-        "clocks": res["bf16"]["clocks"], "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "clocks": res["bf16"]["clocks"], "e2e": e2e,
+        # per call: workspace header, image split, contraction
+        "gpu_launches": 3 * args.steps,
         "cpu_baseline": {"value": kk / cpu_s, "unit": "visibilities/s", "cores": 1,
                          "kind": "oracle", "sample": f"{kk} baselines of the same image, numpy "
                          f"direct sum (Eq. 108), {cpu_s:.1f} s"},
@@ -653,7 +663,8 @@ def run_shadow(args, B, workloads, dev, stream):
         "clocks": clocks,
         "e2e": {"value": n_e2e * points / (w1 - w0), "unit": "boundary points/s",
                 "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": 2 * points * 8},
-        "gpu_launches": len(items) * args.steps,
+        # per spacetime and step: workspace header and the boundary kernel
+        "gpu_launches": 2 * len(items) * args.steps,
     }
     print(json.dumps(line), flush=True)
 
@@ -759,7 +770,7 @@ def run_scan(args, B, workloads, dev, stream):
         "e2e": {"value": n_e2e * n / (w1 - w0), "unit": "spacetimes/s",
                 "h2d_bytes_per_step": int(raw.nbytes),
                 "d2h_bytes_per_step": int(n * (3 * 8 + 4 + 8 * len(theta)))},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,  # one scan kernel per step
     }
     print(json.dumps(line), flush=True)
 
@@ -865,7 +876,8 @@ def run_viscurves(args, B, workloads, dev, stream):
         "e2e": {"value": n_e2e * len(imgs) * n_q / (w1 - w0), "unit": "curve points/s",
                 "h2d_bytes_per_step": int(len(imgs) * n * n * 4 + len(imgs) * n_q * 8),
                 "d2h_bytes_per_step": int(len(imgs) * 2 * n_q * 8)},
-        "gpu_launches": 3 * len(imgs) * args.steps,
+        # per image and step: (u, v) set, header, image split, contraction, reduction
+        "gpu_launches": 5 * len(imgs) * args.steps,
     }
     print(json.dumps(line), flush=True)
 
@@ -972,7 +984,10 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 5; for the millisecond-long visibility, amplitude-"
+                         "curve and 64^2 calls, enough calls to last about a second, so that the "
+                         "clock sampler sees the timed region)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
@@ -998,6 +1013,8 @@ def main():
         return run_profile_case(args)
     if args.warmup < 3:
         args.warmup = 3
+    if args.steps is None:
+        args.steps = {"vis1024": 1000, "viscurves": 300, "kerr64": 30}.get(args.workload, 5)
 
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

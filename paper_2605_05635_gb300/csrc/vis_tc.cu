@@ -77,6 +77,23 @@ __device__ __forceinline__ unsigned long long vis_clock() {
   return t;
 }
 
+// A phase in turns as a 64-bit fixed-point fraction of one turn, so that
+// phases add and scale by integers modulo one turn exactly on the integer
+// pipes (FP64 runs at 1/64 of the FP32 rate here, and the per-block phases
+// of the epilogue and the chunk table would otherwise cost FP64 operations
+// on the critical path).  x is reduced to [0, 1) in FP64 once.
+__device__ __forceinline__ uint64_t turns_fixed(double x) {
+  double f = x - floor(x);
+  if (!(f < 1.0)) f = 0.0;  // x just below an integer rounds up to 1; NaN
+  return (uint64_t)__double2ull_rz(f * 18446744073709551616.0);  // 2^64
+}
+// The phase as half-turns in [-1, 1) (the argument of sincospif): the
+// leading 32 bits read as a signed fraction, rounded to FP32 (within
+// 6e-8 half-turns, as an FP64 phase reduced to [-1, 1] and rounded).
+__device__ __forceinline__ float half_turns(uint64_t t) {
+  return (float)(int32_t)(uint32_t)(t >> 32) * 4.656612873077393e-10f;  // 2^-31
+}
+
 __global__ void vis_begin(VisHdr* h, unsigned long long budget_ns) {
   h->status = 0;
   h->t_start = vis_clock();
@@ -259,7 +276,7 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kStages * kStage + 64);
   volatile int* fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* red = reinterpret_cast<float*>(smem + kStages * kStage + 128);  // [2][128][2]
-  float* tbase = red + 512;                                // [64][nxp / 64] phase table
+  float* tbase = red + 512;  // [nxp / 64][64] phase table (baseline fastest: no bank conflicts)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t uv0 = (int64_t)blockIdx.x * kVisUV;
@@ -295,13 +312,13 @@ __global__ void __launch_bounds__(kVisThreads, 1)
   const int64_t kidx = uv0 + kk;
   const double u = kidx < a.K ? a.uv[2 * kidx] : 0.0;
   const float two_u_dx = (float)(2.0 * u * a.dx);
-  // phase table: 2 u X at the first column of each chunk, reduced mod 2, in FP64
+  // phase table: 2 u X (half-turns, in [-1, 1)) at the first column of each
+  // chunk, from u X = u (x_min + dx / 2) + 64 b u dx in fixed-point turns
   const int nblk = a.nxp / kVisKC;
   if (tid < kGenThreads) {
-    for (int b = seg; b < nblk; b += 4) {
-      double t = 2.0 * u * (a.x_min + (kVisKC * b + 0.5) * a.dx);
-      tbase[kk * nblk + b] = (float)(t - 2.0 * rint(0.5 * t));
-    }
+    const uint64_t ua = turns_fixed(u * (a.x_min + 0.5 * a.dx));
+    const uint64_t ub = turns_fixed(u * a.dx * (double)kVisKC);
+    for (int b = seg; b < nblk; b += 4) tbase[b * kVisUV + kk] = half_turns(ua + (uint64_t)b * ub);
   }
   __syncthreads();
 
@@ -395,6 +412,9 @@ __global__ void __launch_bounds__(kVisThreads, 1)
     const float dv = (float)(2.0 * ev * a.dy);
     float vrot_s, vrot_c;
     sincospif(dv, &vrot_s, &vrot_c);
+    // v Y_j in fixed-point turns: v (y_min + dy / 2) + j v dy
+    const uint64_t va = turns_fixed(ev * (a.y_min + 0.5 * a.dy));
+    const uint64_t vb = turns_fixed(ev * a.dy);
     for (int g = 0; g < total; ++g) {
       const int s = g % kStages;
       const unsigned use = (unsigned)(g / kStages);
@@ -408,7 +428,7 @@ __global__ void __launch_bounds__(kVisThreads, 1)
       // phase tile, hi and lo parts: a sincospif at the segment start, then
       // rotations by one column step (16 steps at most between reseeds)
       {
-        const float t0 = tbase[kk * nblk + c] + (float)(seg * kSeg) * two_u_dx;
+        const float t0 = tbase[c * kVisUV + kk] + (float)(seg * kSeg) * two_u_dx;
         float sn, cs;
         sincospif(t0, &sn, &cs);
         uint16_t ch[kSeg], cl[kSeg], sh[kSeg], sl[kSeg];
@@ -475,10 +495,9 @@ __global__ void __launch_bounds__(kVisThreads, 1)
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           const int jb = jcol0 + cb;
-          // v-phase 2 v Y_jb (mod 2) in FP64, then rotations over the 16 columns
-          const double tvp = 2.0 * ev * (a.y_min + (jb + 0.5) * a.dy);
+          // v-phase 2 v Y_jb at the block start, then rotations over the 16 columns
           float sn, cs;
-          sincospif((float)(tvp - 2.0 * rint(0.5 * tvp)), &sn, &cs);
+          sincospif(half_turns(va + (uint64_t)jb * vb), &sn, &cs);
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const float D = (jb + e < a.ny) ? __uint_as_float(r[e]) : 0.f;
