@@ -277,6 +277,8 @@ bh_status make_params(const bh_spacetime& s, const bh_camera& c, const bh_emissi
   ip.kappa = g.promote_turning;
   ip.sin_o = std::sin(c.incl);
   ip.isin_o = 1.0 / ip.sin_o;
+  ip.md = make_metric_consts<double>(ip);
+  ip.mf = make_metric_consts<float>(ip);
   return BH_OK;
 }
 

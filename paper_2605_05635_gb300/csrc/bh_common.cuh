@@ -17,6 +17,15 @@ namespace bhrt {
 
 constexpr int kMaxLevels = 3;
 
+// Constants of the lapse H(R) (Kerr: 1 - 2/R; Einasto Eq. 9; cored-NFW
+// Eq. 13) in the precision of the right-hand side that reads them.
+template <class T>
+struct MetricConsts {
+  int metric;
+  T chi, chi2, il;      // il = 1/lambda_E
+  T eta_lc, lc, ilc;    // eta*lambda_c, lambda_c, 1/lambda_c
+};
+
 // Per-image constants, computed on the host (Sec. 2.3 horizon, Sec. 3.2
 // ZAMO tetrad scalars, Sec. 5 emission), read by every ray of the image.
 struct alignas(16) ImgParams {
@@ -40,7 +49,27 @@ struct alignas(16) ImgParams {
   double kappa;            // mixed: near-double-root threshold of the radial potential
   int32_t promote_ncross;  // mixed: promote once N_cross reaches this inside demote_R
   int32_t volumetric;      // 1: intensity = Eq. (88) integral (seventh ODE component)
+  // the lapse constants in FP64 and FP32, formed once on the host (their
+  // reciprocals are FP64 divisions, which the kernels would otherwise repeat
+  // at every ray start and in every demotion test)
+  MetricConsts<double> md;
+  MetricConsts<float> mf;
 };
+
+// The lapse constants of an image from its parameters (the host fills
+// ImgParams::md and ::mf with it; the kernels read those copies).
+template <class T>
+__host__ __device__ inline MetricConsts<T> make_metric_consts(const ImgParams& ip) {
+  MetricConsts<T> m;
+  m.metric = ip.metric;
+  m.chi = (T)ip.chi;
+  m.chi2 = (T)(ip.chi * ip.chi);
+  m.il = ip.metric == 1 ? (T)(1.0 / ip.lamE) : T(0);
+  m.lc = (T)ip.lamc;
+  m.ilc = ip.metric == 2 ? (T)(1.0 / ip.lamc) : T(0);
+  m.eta_lc = (T)(ip.eta * ip.lamc);
+  return m;
+}
 
 // Workspace header (first 256 bytes of every workspace).
 struct alignas(256) WsHeader {
@@ -82,13 +111,6 @@ struct LevelRecs {
   int64_t cap;
 };
 
-// Lapse H(R) and dH/dR.  Kerr: 1 - 2/R; Einasto Eq. (9); cored-NFW Eq. (13).
-template <class T>
-struct MetricConsts {
-  int metric;
-  T chi, chi2, il;      // il = 1/lambda_E
-  T eta_lc, lc, ilc;    // eta*lambda_c, lambda_c, 1/lambda_c
-};
 
 
 __device__ __forceinline__ float d_exp(float x) { return __expf(x); }
@@ -228,8 +250,12 @@ static __device__ const double kExp2Tab[32] = {
 // +inf.  Twelve FP64 operations against eighteen for a Taylor series on
 // |r| <= ln2 / 2.
 __device__ __forceinline__ double d_exp(double x) {
-  if (!(x > -708.0)) return x != x ? x : 0.0;
-  if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+  // the range tests only where |x| >= 708 (or x is inf or NaN), found by an
+  // integer test of the leading word: FP64 compares take FP64-pipe slots
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) {
+    if (!(x > -708.0)) return x != x ? x : 0.0;
+    if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+  }
   const double km = fma(x, 46.16624130844683, 6755399441055744.0);  // 32/ln2, 1.5 * 2^52
   const double k = km - 6755399441055744.0;
   const int ik = (int)(unsigned)__double2loint(km);
@@ -381,6 +407,18 @@ __device__ __forceinline__ RayC<T> ray_consts(const MetricConsts<T>& m, T E, T e
   return k;
 }
 
+// x > 0.  For FP64 by the bit pattern on the integer pipes (exact for every
+// non-NaN x, -0 included; a NaN with a clear sign bit passes, and then fails
+// the step's error test).
+template <class T>
+__device__ __forceinline__ bool is_pos(T x) {
+  return x > T(0);
+}
+template <>
+__device__ __forceinline__ bool is_pos<double>(double x) {
+  return __double_as_longlong(x) > 0;
+}
+
 // geo_rhs_sc takes sin(theta) and cos(theta) instead of theta.
 template <class T>
 __device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, const RayC<T>& k, T R, T s,
@@ -412,7 +450,7 @@ __device__ __forceinline__ bool geo_rhs_sc(const MetricConsts<T>& m, const RayC<
   T iS2 = iS * iS;
   d[4] = T(-0.5) * dW_R * iS + W * R * iS2;                       // Eq. (61)
   d[5] = -Q * dQ * iS - W * m.chi2 * s * c * iS2;                 // Eq. (62)
-  return (R > T(0)) && (Dl > T(0));
+  return is_pos(R) && is_pos(Dl);
 }
 template <class T>
 __device__ __forceinline__ bool geo_rhs(const MetricConsts<T>& m, T E, T ell, T R, T th, T pR,

@@ -130,16 +130,14 @@ __device__ __forceinline__ double dense1(double y0, double y1, double hf0, doubl
 }
 
 template <class T>
-__device__ __forceinline__ MetricConsts<T> metric_consts(const ImgParams& ip) {
-  MetricConsts<T> m;
-  m.metric = ip.metric;
-  m.chi = (T)ip.chi;
-  m.chi2 = (T)(ip.chi * ip.chi);
-  m.il = ip.metric == 1 ? (T)(1.0 / ip.lamE) : T(0);
-  m.lc = (T)ip.lamc;
-  m.ilc = ip.metric == 2 ? (T)(1.0 / ip.lamc) : T(0);
-  m.eta_lc = (T)(ip.eta * ip.lamc);
-  return m;
+__device__ __forceinline__ MetricConsts<T> metric_consts(const ImgParams& ip);
+template <>
+__device__ __forceinline__ MetricConsts<double> metric_consts<double>(const ImgParams& ip) {
+  return ip.md;
+}
+template <>
+__device__ __forceinline__ MetricConsts<float> metric_consts<float>(const ImgParams& ip) {
+  return ip.mf;
 }
 
 // 1 / (1 + e^a) without overflow: with t = e^{-|a|} in (0, 1], it is
@@ -438,7 +436,10 @@ __device__ __forceinline__ void ray_init64(const ImgParams& ip, const MetricCons
 // into (0, pi) by (theta, p_th, phi) -> (-theta or 2 pi - theta, -p_th,
 // phi + pi).  Returns true if it reflected.
 __device__ __forceinline__ bool reflect_axis(double& th, double& pth, double& ph) {
-  if (th >= 0.0 && th <= kPi) return false;
+  // 0 <= th <= pi as an unsigned compare of the bit pattern (+0 .. pi, and
+  // -0), on the integer pipes; negative values and NaN order above pi
+  const unsigned long long u = (unsigned long long)__double_as_longlong(th);
+  if (u <= 0x400921FB54442D18ull || u == 0x8000000000000000ull) return false;
   th = th < 0.0 ? -th : kTwoPi - th;
   pth = -pth;
   ph += kPi;
@@ -476,6 +477,16 @@ __device__ __forceinline__ float f32_trunc(double x) {
   const int sign = hi & (int)0x80000000;
   const int mag = e <= 0 ? 0 : (e >= 255 ? 0x7f7fffff : ((e << 23) | ((hi & 0xfffff) << 3)));
   return __int_as_float(sign | mag);
+}
+
+// A normal, nonzero float widened to double by bit manipulation on the
+// integer pipes (exact; the step factors lie in [0.2, 10]).
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
+                               ((unsigned long long)(((b >> 23) & 0xff) + 896) << 52) |
+                               ((unsigned long long)(b & 0x7fffff) << 29);
+  return __longlong_as_double((long long)d);
 }
 
 // One component's squared scaled error (h e_i / sc_i)^2,
@@ -583,7 +594,7 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   float err = sqrtf(err2 / (vol ? 7.f : 6.f));
   r.steps++;
   if (bad || !(err <= 1.f)) {
-    r.h = bad ? 0.5 * h : h * (double)step_factor(err, true);
+    r.h = bad ? 0.5 * h : h * f64_of_f32(step_factor(err, true));
     r.rejected = true;
     r.nrej++;
     return r.steps >= ip.max_steps ? 3 : 0;
@@ -594,8 +605,11 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     r.fI = kI;
   }
   if (kEvents) {
-    const double s0 = r.y[2] - kHalfPi, s1 = y1[2] - kHalfPi;
-    if ((s0 > 0.0 && s1 <= 0.0) || (s0 < 0.0 && s1 >= 0.0)) {
+    // sign tests of theta - pi/2 on the bit patterns (integer pipes; a
+    // difference of two doubles is never -0 under round-to-nearest)
+    const long long s0 = __double_as_longlong(r.y[2] - kHalfPi);
+    const long long s1 = __double_as_longlong(y1[2] - kHalfPi);
+    if ((s0 > 0 && s1 <= 0) || (s0 < 0 && s1 >= 0)) {
       double hf0[6], hf1[6], hd[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -649,7 +663,7 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   if (hdv > r.hdrift) r.hdrift = hdv;
   if (r.y[1] < ip.R_cap) return 2;
   if (r.y[1] > ip.R_esc) return 1;
-  r.h = h * (double)step_factor(err, r.rejected);
+  r.h = h * f64_of_f32(step_factor(err, r.rejected));
   if (vol) r.h = layer_cap(ip.H0, ip.hh, r.y[1], r.y[2], r.f[1], r.f[2], r.h);
   r.rejected = false;
   return r.steps >= ip.max_steps ? 3 : 0;
