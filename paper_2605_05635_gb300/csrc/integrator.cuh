@@ -203,6 +203,60 @@ static __device__ __noinline__ double vol_source64(const ImgParams& ip, MetricCo
   return g * g * g * ip.j0 * d_exp(lnj) * tin * tout;
 }
 
+// Redshift of a prograde circular emitter (Eqs. 89-91), FP32.
+__device__ __forceinline__ bool emitter_g_f(const MetricConsts<float>& m, float R, float E,
+                                            float ell, float& g) {
+  float H, dH;
+  lapse(m, R, __fdividef(1.f, R), H, dH);
+  const float den = 2.f * R - m.chi2 * dH, disc = 2.f * R * dH;
+  if (!(disc >= 0.f) || den == 0.f) return false;
+  const float W = __fdividef(-m.chi * dH + sqrtf(disc), den);
+  const float gtt = -H, gtp = -m.chi * (1.f - H), gpp = R * R + m.chi2 + m.chi2 * (1.f - H);
+  const float norm = -(gtt + 2.f * W * gtp + W * W * gpp);
+  if (!(norm > 0.f)) return false;
+  g = __fdividef(sqrtf(norm), E - W * ell);
+  return true;
+}
+
+// Source of the volumetric intensity (Eq. 88) in FP32: g^3 j at (R, theta),
+// theta given as dth = theta - pi/2 (see dtheta_eq), as vol_source64 (mirror
+// point past the polar axis, emitter at the cylindrical radius rho, tapers as
+// logistic functions), from the image's FP32 emission constants.
+// 1 / (1 + e^a) without overflow (see logistic_neg), FP32.
+__device__ __forceinline__ float logistic_neg_f(float a) {
+  const float t = __expf(-fabsf(a));
+  const float s = __fdividef(1.f, 1.f + t);
+  return a >= 0.f ? t * s : s;
+}
+
+static __device__ __noinline__ float vol_source32(const ImgParams& ip, MetricConsts<float> m,
+                                                  float E, float ell, float R, float dth) {
+  float s, c;
+  d_sincos(dth, &s, &c);
+  const float rho = R * fabsf(c), z = -R * s;
+  float g;
+  if (!(rho > 0.f) || !emitter_g_f(m, rho, E, ell, g)) return 0.f;
+  const float* v = ip.vf;  // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
+  const float zH = __fdividef(z, v[0] + v[1] * rho);                    // Eq. (84)
+  const float tin = logistic_neg_f(-2.f * (rho - v[2]) * v[3]);   // Eq. (85)
+  const float tout = logistic_neg_f(2.f * (rho - v[5]) * v[4]);   // Eq. (86)
+  const float lnj = -v[6] * __logf(rho * v[9]) - (rho - v[2]) * v[7] - 0.5f * zH * zH;
+  return g * g * g * v[8] * __expf(lnj) * tin * tout;                    // Eq. (83)
+}
+
+// The volumetric source for an FP64 state in the mixed path's promoted pass:
+// the FP32 evaluation of the FP32 legs (vol_source32) from E, ell, R and
+// theta - pi/2 formed in FP64 and rounded.  The source enters only the
+// intensity integral, which the mixed path holds to its bar, not the
+// trajectory that the promotion protects; the all-FP64 path keeps
+// vol_source64.
+static __device__ __noinline__ double vol_source_mx(const ImgParams& ip, double E, double ell,
+                                                    double R, double th) {
+  return (double)vol_source32(ip, metric_consts<float>(ip), __double2float_rn(E),
+                              __double2float_rn(ell), __double2float_rn(R),
+                              __double2float_rn(th - kHalfPi));
+}
+
 // Volumetric mode (reading, as in the oracle): a step that may come within
 // 5 H(rho) of the equatorial plane advances z by at most H(rho) / 2, so
 // that the stages sample the Gaussian layer however thin it is.
@@ -532,6 +586,8 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   // volumetric mode: the intensity integral is a seventh component whose
   // derivative g^3 j depends on the state only (kI, sums s5I and seI)
   const bool vol = kVol && ip.volumetric != 0;
+  // the mixed path's promoted pass takes the source in FP32 (vol_source_mx)
+  const bool src32 = vol && a.source == 1;
   double kI = kVol ? r.fI : 0.0, s5I = 0.0, seI = 0.0;
   const RayC<double> kc = ray_consts(m, r.E, r.ell);
 #pragma unroll 1
@@ -572,7 +628,9 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
     d_sincos(ys[1], &sth, &cth);
     bool ok = geo_rhs_sc(m, kc, ys[0], sth, cth, ys[2], ys[3], k, W, P2oD);
     bad |= !ok;
-    if (vol) kI = vol_source64(ip, m, r.E, r.ell, ys[0], ys[1]);
+    if (vol)
+      kI = src32 ? vol_source_mx(ip, r.E, r.ell, ys[0], ys[1])
+                 : vol_source64(ip, m, r.E, r.ell, ys[0], ys[1]);
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
 #pragma unroll
@@ -655,7 +713,9 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   }
   if (reflect_axis(r.y[2], r.y[5], r.y[3])) {
     rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
-    if (vol) r.fI = vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]);
+    if (vol)
+      r.fI = src32 ? vol_source_mx(ip, r.E, r.ell, r.y[1], r.y[2])
+                   : vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]);
   }
   // null-constraint monitor at the new point (stage 7 = new point, FSAL)
   // (a monitor to a few digits: FP32 from truncated operands, off the FP64 pipe)
@@ -725,7 +785,8 @@ __device__ __forceinline__ void resume64(const ImgParams& ip, const SpillRec& s,
   r.steps = s.steps;
   r.xpend = false;
   rhs_f64_into(m, r.E, r.ell, r.y[1], r.y[2], r.y[4], r.y[5], r.f);
-  r.fI = ip.volumetric ? vol_source64(ip, m, r.E, r.ell, r.y[1], r.y[2]) : 0.0;
+  // a resumed ray is in the mixed path's promoted pass: FP32 source
+  r.fI = ip.volumetric ? vol_source_mx(ip, r.E, r.ell, r.y[1], r.y[2]) : 0.0;
 }
 
 // Carter-type constant K = p_th^2 + Q^2, Q = ell/sin(theta) - chi E sin(theta)

@@ -67,21 +67,6 @@ __device__ __forceinline__ void rhs_f32_into(const MetricConsts<float>& m, float
   for (int i = 0; i < 6; ++i) d[i] = o.d[i];
 }
 
-// Redshift of a prograde circular emitter (Eqs. 89-91), FP32.
-__device__ __forceinline__ bool emitter_g_f(const MetricConsts<float>& m, float R, float E,
-                                            float ell, float& g) {
-  float H, dH;
-  lapse(m, R, __fdividef(1.f, R), H, dH);
-  const float den = 2.f * R - m.chi2 * dH, disc = 2.f * R * dH;
-  if (!(disc >= 0.f) || den == 0.f) return false;
-  const float W = __fdividef(-m.chi * dH + sqrtf(disc), den);
-  const float gtt = -H, gtp = -m.chi * (1.f - H), gpp = R * R + m.chi2 + m.chi2 * (1.f - H);
-  const float norm = -(gtt + 2.f * W * gtp + W * W * gpp);
-  if (!(norm > 0.f)) return false;
-  g = __fdividef(sqrtf(norm), E - W * ell);
-  return true;
-}
-
 // Step-size factor of the FP32 steps: safety 0.8 (0.9 in the FP64 steps),
 // clamp [0.2, 10], no growth right after a rejection.  The FP32 error
 // estimate fluctuates with rounding, so steps sized for 0.9 of the tolerance
@@ -106,32 +91,6 @@ constexpr float kPiHi = 3.1415927410125732421875f;
 // keeps its relative accuracy, which theta rounded to one float would not.
 __device__ __forceinline__ float dtheta_eq(float th_h, float th_l, float extra) {
   return __fadd_rn(__fsub_rn(th_h, kHalfPiHi), __fsub_rn(th_l, kHalfPiLo) + extra);
-}
-
-// Source of the volumetric intensity (Eq. 88) in FP32: g^3 j at (R, theta),
-// theta given as dth = theta - pi/2 (see dtheta_eq), as vol_source64 (mirror
-// point past the polar axis, emitter at the cylindrical radius rho, tapers as
-// logistic functions), from the image's FP32 emission constants.
-// 1 / (1 + e^a) without overflow (see logistic_neg), FP32.
-__device__ __forceinline__ float logistic_neg_f(float a) {
-  const float t = __expf(-fabsf(a));
-  const float s = __fdividef(1.f, 1.f + t);
-  return a >= 0.f ? t * s : s;
-}
-
-static __device__ __noinline__ float vol_source32(const ImgParams& ip, MetricConsts<float> m,
-                                                  float E, float ell, float R, float dth) {
-  float s, c;
-  d_sincos(dth, &s, &c);
-  const float rho = R * fabsf(c), z = -R * s;
-  float g;
-  if (!(rho > 0.f) || !emitter_g_f(m, rho, E, ell, g)) return 0.f;
-  const float* v = ip.vf;  // H0, hh, R_in, 1/sig_in, 1/sig_out, R_out, p, 1/R_s, j0, 1/R_in
-  const float zH = __fdividef(z, v[0] + v[1] * rho);                    // Eq. (84)
-  const float tin = logistic_neg_f(-2.f * (rho - v[2]) * v[3]);   // Eq. (85)
-  const float tout = logistic_neg_f(2.f * (rho - v[5]) * v[4]);   // Eq. (86)
-  const float lnj = -v[6] * __logf(rho * v[9]) - (rho - v[2]) * v[7] - 0.5f * zH * zH;
-  return g * g * g * v[8] * __expf(lnj) * tin * tout;                    // Eq. (83)
 }
 
 struct RayMx {
