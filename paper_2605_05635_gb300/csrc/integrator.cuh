@@ -721,8 +721,13 @@ __device__ __forceinline__ int ray_step64(const ImgParams& ip, const MetricConst
   // (a monitor to a few digits: FP32 from truncated operands, off the FP64 pipe)
   float hdv = __fdividef(f32_trunc(fabs(W)), f32_trunc(P2oD));
   if (hdv > r.hdrift) r.hdrift = hdv;
-  if (r.y[1] < ip.R_cap) return 2;
-  if (r.y[1] > ip.R_esc) return 1;
+  // an accepted state is never NaN (a NaN stage makes the error norm
+  // infinite), so R compares with the radii by bit pattern (integer pipes):
+  // for R >= 0 the order of the patterns is the order of the values, and a
+  // negative R has a negative pattern
+  const long long rb = __double_as_longlong(r.y[1]);
+  if (rb < __double_as_longlong(ip.R_cap)) return 2;
+  if (rb > __double_as_longlong(ip.R_esc)) return 1;
   r.h = h * f64_of_f32(step_factor(err, r.rejected));
   if (vol) r.h = layer_cap(ip.H0, ip.hh, r.y[1], r.y[2], r.f[1], r.f[2], r.h);
   r.rejected = false;

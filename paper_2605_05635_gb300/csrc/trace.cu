@@ -105,8 +105,10 @@ __global__ void __launch_bounds__(128, MinBlocks) trace_fp64_kernel(TraceArgs a)
       w_rej += (unsigned long long)(r.nrej - rej0);
       // outgoing beyond the strong-field zone, or away from the double root
       // of its radial potential: finish in FP32
-      spill = !term && a.allow_spill && r.nacc != acc0 && r.y[4] > 0.0 &&
-              (r.y[1] > ip->demote_R ||
+      // (p_R > 0 and R > demote_R as bit-pattern compares: the accepted
+      // state is not NaN and R is positive)
+      spill = !term && a.allow_spill && r.nacc != acc0 && __double_as_longlong(r.y[4]) > 0 &&
+              (__double_as_longlong(r.y[1]) > __double_as_longlong(ip->demote_R) ||
                (ip->kappa > 0.0 && past_double_root(*ip, r.E, r.ell, r.y[1], r.y[4])));
     }
     // parked crossings: evaluated together once kXFlushLanes lanes hold one,
