@@ -168,8 +168,9 @@ __device__ __forceinline__ void d_sincos(double x, double* s, double* c) {
   pc = fma(pc, r2, -0.5);
   const double cr = fma(pc, r2, 1.0);
   const double so = (iq & 1) ? cr : sr, co = (iq & 1) ? sr : cr;
-  *s = (iq & 2) ? -so : so;
-  *c = ((iq + 1) & 2) ? -co : co;
+  // quadrant signs by flipping the sign bit (integer pipe, not an FP64 negation)
+  *s = __longlong_as_double(__double_as_longlong(so) ^ ((long long)(iq & 2) << 62));
+  *c = __longlong_as_double(__double_as_longlong(co) ^ ((long long)((iq + 1) & 2) << 62));
 }
 // FP32 sine and cosine without a slow path (the polar angle and the trial
 // stages around it stay within a few radians): Cody & Waite reduction by
