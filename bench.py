@@ -103,25 +103,40 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines[self.first:]:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return None
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarise_clocks(self.lines[self.first:])
+
+
+def summarise_clocks(lines):
+    """Median SM clock, maximum clock and the throttle reasons seen in the
+    nvidia-smi CSV lines (index, clocks.sm, clocks.max.sm, power.draw,
+    active reasons, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
+    sw_power_cap); None without a sample."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def default_steps(workload: str) -> int:
+    """Timed steps when --steps is not given: 5, or enough of the
+    millisecond-long calls to last about a second (so that the clock sampler
+    has samples inside the timed region)."""
+    return {"vis1024": 1000, "viscurves": 300, "kerr64": 30}.get(workload, 5)
 
 
 def aggregate_ranks(rays: float, ms: float, world: int, device):
@@ -1014,7 +1029,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.steps is None:
-        args.steps = {"vis1024": 1000, "viscurves": 300, "kerr64": 30}.get(args.workload, 5)
+        args.steps = default_steps(args.workload)
 
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

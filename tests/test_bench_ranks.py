@@ -73,3 +73,27 @@ def test_added_workload_generators():
     assert all(d["nx"] == 1024 and d["chi"] == 0.95 and d["levels"] == 3 for d in imgs)
     vol = workloads.sweep_512(precision=1, volumetric=True)
     assert all(d["volumetric"] == 1 for d in vol) and len(vol) == 6
+
+
+def test_clock_summary_and_step_defaults():
+    """The clock record is the median SM clock of the samples with the
+    throttle reasons they show; a sample with an unreadable clock is skipped
+    and no sample gives None. Millisecond-long workloads default to enough
+    timed calls for the sampler to see the timed region."""
+    import bench
+    lines = ["0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage"]
+    c = bench.summarise_clocks(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    hot = bench.summarise_clocks(["0, 1500, 2070, 1400, 0x8, Not Active, Active, Not Active, "
+                                  "Not Active"])
+    assert hot["reasons"] == ["hw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    assert bench.summarise_clocks([]) is None
+    assert bench.default_steps("sweep512") == 5
+    assert bench.default_steps("vis1024") * 0.7e-3 >= 0.5      # about 0.75 ms per call
+    assert bench.default_steps("viscurves") * 2.9e-3 >= 0.5
+    assert bench.default_steps("kerr64") * 30e-3 >= 0.5
