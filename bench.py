@@ -46,7 +46,7 @@ KEYS_CAP = 1 << 23                 # refinement-pattern keys kept per image
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum over the
 # kernel's launches of one plan launch); to be retaken whenever a trace kernel
 # changes.  Not measured for the volumetric layer, which reports null.
-TRAFFIC_PER_STEP = {}
+TRAFFIC_PER_STEP = {"trace_fp64_kernel": 2.15e9, "trace_mixed_kernel": 2.16e9}
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
@@ -326,15 +326,23 @@ def run_sweep96(args, B, workloads, dev, stream):
     images_per_s = len(items) / (ms / 1e3)
     steps32, ms32 = st["accepted_fp32"], st["fp32_ms"]
     steps64, ms64 = st["accepted_fp64"], st["fp64_ms"]
+    tot_ms = ms32 + ms64
+
+    def roof(steps, kms, peak, kern, lanes):
+        ach = steps * FLOP_PER_STEP / (kms / 1e3) / 1e12 if kms > 0 else 0.0
+        return {"bound": "alu", "achieved": ach, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": ach * 1e12 / peak, "traffic": None, "kernel": kern,
+                "kernel_share_of_step": kms / tot_ms if tot_ms > 0 else None,
+                "accepted_steps": steps, "flop_per_accepted_step": FLOP_PER_STEP,
+                "lane_util": st[lanes]}
+    r64 = roof(steps64, ms64, FP64_PEAK_FLOPS, "trace_fp64_kernel", "lane_util_fp64")
     if prec == B.FP64:
-        flops, kms, peak, kern = steps64 * FLOP_PER_STEP, ms64, FP64_PEAK_FLOPS, "trace_fp64_kernel"
+        roofline = r64
     else:
-        flops, kms, peak, kern = steps32 * FLOP_PER_STEP, ms32, FP32_PEAK_FLOPS, "trace_mixed_kernel"
-    achieved = flops / (kms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved * 1e12 / peak, "traffic": None, "kernel": kern,
-                "kernel_share_of_step": kms / (st["fp32_ms"] + st["fp64_ms"]) if kms > 0 else None,
-                "lane_util": st["lane_util_fp32" if prec == B.MIXED else "lane_util_fp64"]}
+        # the dominant trace kernel of the step, the other alongside
+        r32 = roof(steps32, ms32, FP32_PEAK_FLOPS, "trace_mixed_kernel", "lane_util_fp32")
+        roofline, other = (r64, r32) if ms64 >= ms32 else (r32, r64)
+        roofline = dict(roofline, other_trace_kernel=other)
     # single-image FP64 tracing of a sample (one image per spin, all metrics)
     sample = list(range(0, len(base), 12))
     t_single, errs, p999, changed = [], [], [], 0
@@ -480,7 +488,7 @@ def run_adjoint(args, B, workloads, dev, stream):
     flat_keys = {0: "chi", 1: "incl", 4: "j0", 5: "p", 6: "R_s", 7: "sigma_in", 8: "sigma_out",
                  9: "R_out"}
     uv8 = workloads.uv_points(8, seed=20260514)
-    rows, times, fwd_times = [], [], []
+    rows, times, fwd_times, clocks = [], [], [], []
     for metric in (workloads.KERR, workloads.CNFW):
         flat = dict(workloads.kerr_64(), metric=metric, chi=0.7, incl=math.radians(50.0), nx=256,
                     ny=256, x_min=-12.0, x_max=12.0, y_min=-12.0, y_max=12.0, levels=1,
@@ -492,22 +500,29 @@ def run_adjoint(args, B, workloads, dev, stream):
         w = torch.from_numpy(rng.normal(size=(256, 256))).float().to(dev)
         st, cam, em, it = B.from_flat(flat)
         with torch.cuda.stream(stream):
-            B.trace_backward(st, cam, em, it, dL_dI=w, stream=stream)       # warm-up
+            for _ in range(args.warmup):
+                B.trace_backward(st, cam, em, it, dL_dI=w, stream=stream)
             torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                grad, diag, img = B.trace_backward(st, cam, em, it, dL_dI=w, stream=stream)
-            t1 = time.perf_counter()
-            times.append((t1 - t0) / args.steps)
+            sampler = ClockSampler(dev.index or 0)
+            sampler.start()
+            res = {}
+
+            def grad_call():
+                res["g"] = B.trace_backward(st, cam, em, it, dL_dI=w, stream=stream)
+            times.append(_events_ms(stream, grad_call, args.steps) / 1e3)
+            clocks.append(sampler.stop())
+            grad, diag, img = res["g"]
 
             def loss(d):
                 out = B.trace_batch([B.from_flat(d)], device=dev, stream=stream)[0]
                 return float((out["I"].double() * w.double()).sum())
+            L0 = loss(flat)          # warm-up (workspace allocation)
             torch.cuda.synchronize(dev)
             f0 = time.perf_counter()
-            L0 = loss(flat)
+            for _ in range(3):
+                L0 = loss(flat)
             torch.cuda.synchronize(dev)
-            fwd_times.append(time.perf_counter() - f0)
+            fwd_times.append((time.perf_counter() - f0) / 3)
             fd = {}
             for k, key in keys.items():
                 x0 = flat[key]
@@ -520,15 +535,25 @@ def run_adjoint(args, B, workloads, dev, stream):
                      "free_fd": fd, "rel_err_vs_free_fd": rel,
                      "median_rel_err_vs_free_fd": float(np.median(list(rel.values())))})
     t = sum(times) / len(times)
+    seen = [c for c in clocks if c]
     line = {
         "metric": METRIC_ADJ, "value": 1.0 / t, "unit": "gradients/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": 1, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_ADJ, "nx": 256, "ny": 256, "levels": 1,
                    "parallelism": "dp1"},
         "forward_fp64_ms": 1e3 * sum(fwd_times) / len(fwd_times),
         "backward_over_forward": t / (sum(fwd_times) / len(fwd_times)),
         "per_metric": rows,
+        "clocks": ({"sm_mhz": min(c["sm_mhz"] for c in seen),
+                    "sm_max_mhz": max(c["sm_max_mhz"] for c in seen),
+                    "reasons": sorted({x for c in seen for x in c["reasons"]}),
+                    "samples": sum(c["samples"] for c in seen)} if seen else None),
+        # per gradient: the forward plan (workspace header, level-0 and level-1
+        # traces, refinement marking, assembly), image moments, radial
+        # profile, per-pixel adjoint and the ray adjoint; both spacetimes
+        "gpu_launches": 9 * args.steps * 2,
         "note": ("the adjoint differentiates the algorithm with its adaptive decisions frozen; "
                  "free differences of the pixel-sampled image also contain the motion of class "
                  "boundaries (shadow edge, photon-ring orders) across pixels, so they agree only "
@@ -557,10 +582,16 @@ def run_kerr64(args, B, workloads, dev, stream):
         for _ in range(args.warmup):
             plan.launch(stream=stream)
         plan.check(stream)
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
         ms = _events_ms(stream, lambda: plan.launch(stream=stream), args.steps)
+        clocks = sampler.stop()
         st = plan.stats(stream)
     rays = sum(st["rays"])
+    steps_acc = st["accepted_fp64"]
     plan.close()
+    ach = steps_acc * FLOP_PER_STEP / (ms / 1e3) / 1e12
     oracle.build()
     P = oracle.problem(**{k: v for k, v in flat.items() if k in oracle.DEFAULTS})
     t0 = time.perf_counter()
@@ -578,6 +609,12 @@ def run_kerr64(args, B, workloads, dev, stream):
         "cpu_baseline": {"value": rays / t_or, "unit": "rays/s", "cores": cores,
                          "kind": "oracle", "sample": f"the whole image, {t_or:.2f} s"},
         "oracle_seconds_for_image": t_or,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_FLOPS / 1e12,
+                     "unit": "TFLOP/s", "frac": ach * 1e12 / FP64_PEAK_FLOPS, "traffic": None,
+                     "kernel": "trace_fp64_kernel", "flop_per_accepted_step": FLOP_PER_STEP,
+                     "accepted_steps": steps_acc,
+                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
+        "clocks": clocks, "gpu_launches": st["kernel_launches"] * args.steps,
     }
     print(json.dumps(line), flush=True)
 
