@@ -112,7 +112,10 @@ typedef struct {
                          no timelike orbit exists, and steps that may come
                          within 5 H of the plane advancing z by at most H/2.
                          I_n planes stay 0; H0 > 0 and h >= 0 required.
-                         Not differentiable by bh_trace_backward.          */
+                         The all-FP64 path evaluates the source g^3 j in
+                         FP64; the mixed path evaluates it in FP32 on every
+                         leg (the promoted FP64 steps keep an FP64
+                         geodesic).  Not differentiable by bh_trace_backward. */
   double j0, p, R_s;  /* normalisation, radial power, radial scale (Eq. 83) */
   double sigma_in, sigma_out, R_out; /* tapers, Eqs. (85)-(86)             */
   double dR_in;       /* used when r_in_mode == 1                           */

@@ -9,15 +9,18 @@
 //   - the state is carried as an unevaluated sum hi + lo of two floats, so
 //     each step's increment is added with ~48-bit precision (the transverse
 //     position at R ~ 1000 would otherwise drift by ~R 1e-7 per step);
-//   - launch, constants of motion (E, ell), starting step, crossing roots,
-//     transfer maps, redshift and emissivity run in FP64;
+//   - the launch and the constants of motion (E, ell) are formed in FP64
+//     and rounded; the starting step, crossing roots, transfer maps,
+//     redshift, emissivity and the volumetric source run in FP32, so the
+//     stepping loop issues no FP64 instruction;
 //   - a ray is promoted to the FP64 kernel when it comes within promote_R of
-//     the horizon or, winding to image order n >= 2 (N_cross >= 3, Sec. 4.2),
-//     is inside demote_R; the FP64
-//     pass hands it back once it is outgoing beyond demote_R, and a second
-//     FP32 pass (no further promotion) finishes it.  Promotion is a hand-off
-//     through a queue rather than a per-lane branch, so warps never mix FP64
-//     and FP32 steps.
+//     the horizon, when, winding to image order n >= 2 (N_cross >= 3,
+//     Sec. 4.2), it is inside demote_R, or when it nears a double root of
+//     its radial potential (kappa); the FP64 pass hands it back once it is
+//     outgoing beyond demote_R or past that root, and a second FP32 pass (no
+//     further promotion) finishes it.  Promotion is a hand-off through a
+//     queue rather than a per-lane branch, so warps never mix FP64 and FP32
+//     steps.
 #include <cuda_runtime.h>
 
 #include "integrator.cuh"
