@@ -143,12 +143,13 @@ typedef struct {
                            Hamiltonian (Eqs. 56-59), Rr(R) = P^2 - Delta K =
                            (Delta p_R)^2, P = (R^2 + chi^2) E - chi ell and K
                            the Carter-type constant p_th^2 + Q^2, a ray inside
-                           R = 5 takes FP64 steps (until outgoing beyond
-                           R = 5) once Rr < kappa P^2 and Rr'^2 <
-                           2 kappa Rr'' P^2 (Rr'' with Kerr's Delta'' = 2):
-                           it is within kappa of a double root of Rr, i.e.
-                           near the photon orbit, about to turn or to
-                           plunge.  kappa = promote_turning in [0, 1];
+                           R = 5 takes FP64 steps once Rr < kappa P^2 and
+                           Rr'^2 < 2 kappa Rr'' P^2 (Rr'' with Kerr's
+                           Delta'' = 2): it is within kappa of a double root
+                           of Rr, i.e. near the photon orbit, about to turn
+                           or to plunge; it returns to FP32 once outgoing
+                           beyond R = 5 or with Rr > 1.2 kappa P^2 (past the
+                           root).  kappa = promote_turning in [0, 1];
                            0 = off.  Every FP32 -> FP64 hand-off also puts
                            p_th and p_R back on the ray's FP64 constants
                            E, ell (Eq. 48) and K from the launch, with
