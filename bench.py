@@ -46,7 +46,7 @@ KEYS_CAP = 1 << 23                 # refinement-pattern keys kept per image
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum over the
 # kernel's launches of one plan launch); to be retaken whenever a trace kernel
 # changes.  Not measured for the volumetric layer, which reports null.
-TRAFFIC_PER_STEP = {}
+TRAFFIC_PER_STEP = {"trace_fp64_kernel": 2.14e9, "trace_mixed_kernel": 2.15e9}
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
